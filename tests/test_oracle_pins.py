@@ -1,0 +1,517 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own code: closed forms,
+brute-force recomputation (tests/brute.py), exhaustive partition search,
+hand-worked fixtures (tests/golden/) and invariants stated by the paper.
+"""
+from __future__ import annotations
+
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2405_11658_gb300 import synth as S
+from tests import brute as B
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def rand_graph(n, p, seed, wmax=3, loops=False):
+    rng = np.random.default_rng(seed)
+    off, idx, w = S.erdos_renyi(n, p, seed, wmax=wmax)
+    if not loops:
+        return off, idx, w.astype(np.int64)
+    # add a few self-loops, stored once (Sec. 3: w_ii counted once in K_i and 2m)
+    src = np.repeat(np.arange(n), np.diff(off))
+    lv = rng.choice(n, size=max(1, n // 4), replace=False)
+    src = np.concatenate([src, lv])
+    dst = np.concatenate([idx.astype(np.int64), lv])
+    ww = np.concatenate([w.astype(np.int64), rng.integers(1, wmax + 1, size=len(lv))])
+    o = np.lexsort((dst, src))
+    src, dst, ww = src[o], dst[o], ww[o]
+    off2 = np.zeros(n + 1, np.int64)
+    off2[1:] = np.cumsum(np.bincount(src, minlength=n))
+    return off2, dst.astype(np.int32), ww
+
+
+# --------------------------------------------------------------------------
+# Eq. 1
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("gamma", [1.0, 0.5, 1.25])
+def test_modularity_matches_newman_form(seed, gamma):
+    off, idx, w = rand_graph(14, 0.3, seed, wmax=4, loops=(seed % 2 == 1))
+    rng = np.random.default_rng(100 + seed)
+    C = rng.integers(0, 5, size=14).astype(np.int32)
+    qv, num = O.modularity(off, idx, w, C, gamma)
+    p, q = O.gamma_ratio(gamma)
+    A = B.dense(off, idx, w)
+    expect = B.q_newman(A, C.tolist(), p, q)
+    two_m = sum(sum(r) for r in A)
+    assert Fraction(num, q * two_m * two_m) == expect
+    assert qv == pytest.approx(float(expect), abs=1e-15)
+
+
+def test_gamma_ratio_exact():
+    assert O.gamma_ratio(1.0) == (1, 1)
+    assert O.gamma_ratio(0.75) == (3, 4)
+    assert O.gamma_ratio(2.0) == (2, 1)
+    with pytest.raises(ValueError):
+        O.gamma_ratio(0.1)  # not a multiple of 2^-20
+    with pytest.raises(ValueError):
+        O.gamma_ratio(-1.0)
+
+
+@pytest.mark.parametrize("case", gold("ring_of_cliques.json")["cases"])
+def test_ring_of_cliques_closed_form(case):
+    r, k = case["r"], case["k"]
+    off, idx, w = S.ring_of_cliques(r, k)
+    truth = np.arange(r * k) // k
+    qv, num = O.modularity(off, idx, w, truth)
+    two_m = int(w.sum())
+    assert Fraction(num, two_m * two_m) == Fraction(case["q_num"], case["q_den"])
+    for sched in (O.SCHED_DET, O.SCHED_GS):
+        res = O.static(off, idx, w, O.LeidenOpts(sched=sched))
+        assert np.array_equal(res.membership, truth)
+        assert res.q == pytest.approx(case["q_num"] / case["q_den"], abs=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Eq. 2: the scaled integer delta-modularity equals Q(after) - Q(before)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("gamma", [1.0, 0.5, 1.5])
+def test_delta_modularity_equals_difference(seed, gamma):
+    n = 9
+    off, idx, w = rand_graph(n, 0.45, 10 + seed, wmax=3, loops=(seed % 2 == 0))
+    rng = np.random.default_rng(seed)
+    C = rng.integers(0, 4, size=n).astype(np.int32)
+    p, q = O.gamma_ratio(gamma)
+    A = B.dense(off, idx, w)
+    two_m = sum(sum(r) for r in A)
+    base = B.q_newman(A, C.tolist(), p, q)
+    for i in range(n):
+        for c in range(n):
+            if c == C[i]:
+                continue
+            D = C.tolist()
+            D[i] = c
+            s = O.move_score(off, idx, w, C, i, c, p, q)
+            assert Fraction(s, 2 * q) / Fraction(two_m * two_m, 4) == \
+                B.q_newman(A, D, p, q) - base, (i, c)
+
+
+# --------------------------------------------------------------------------
+# Whole Leiden vs exhaustive partition search (n <= 10)
+# --------------------------------------------------------------------------
+def two_cliques_weak_link(k1, k2, extra=()):
+    n = k1 + k2
+    us, vs = [], []
+    for base, k in ((0, k1), (k1, k2)):
+        for x in range(k):
+            for y in range(x + 1, k):
+                us.append(base + x)
+                vs.append(base + y)
+    us.append(k1 - 1)
+    vs.append(k1)
+    for a, b in extra:
+        us.append(a)
+        vs.append(b)
+    return S.edges_to_csr(n, us, vs)
+
+
+def three_cliques(k):
+    us, vs = [], []
+    for c in range(3):
+        for x in range(k):
+            for y in range(x + 1, k):
+                us.append(c * k + x)
+                vs.append(c * k + y)
+    us += [k - 1, 2 * k - 1, 3 * k - 1]
+    vs += [k, 2 * k, 0]
+    return S.edges_to_csr(3 * k, us, vs)
+
+
+@pytest.mark.parametrize("name,g", [
+    ("K5+K5", two_cliques_weak_link(5, 5)),
+    ("K4+K6", two_cliques_weak_link(4, 6)),
+    ("3xK3", three_cliques(3)),
+])
+def test_planted_optimum_found_exactly(name, g):
+    off, idx, w = g
+    A = B.dense(off, idx, w)
+    qopt, part = B.exhaustive_best(A)
+    for sched in (O.SCHED_DET, O.SCHED_GS):
+        res = O.static(off, idx, w, O.LeidenOpts(sched=sched))
+        assert np.array_equal(res.membership, O.canonical(part)), name
+        assert B.q_newman(A, res.membership.tolist()) == qopt
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_leiden_never_beats_exhaustive_optimum(seed):
+    n = 9 + seed % 2
+    off, idx, w = rand_graph(n, 0.35, 200 + seed, wmax=2)
+    A = B.dense(off, idx, w)
+    qopt, _ = B.exhaustive_best(A)
+    for sched in (O.SCHED_DET, O.SCHED_GS):
+        res = O.static(off, idx, w, O.LeidenOpts(sched=sched))
+        got = B.q_newman(A, res.membership.tolist())
+        assert got <= qopt
+        assert float(got) == pytest.approx(res.q, abs=1e-12)
+        assert B.all_connected(off, idx, res.membership)
+
+
+def test_restricted_growth_counts_bell_numbers():
+    bell = [1, 2, 5, 15, 52, 203, 877, 4140, 21147, 115975]
+    for n in range(1, 11):
+        assert len(B.restricted_growth(n)) == bell[n - 1]
+
+
+# --------------------------------------------------------------------------
+# Phase invariants
+# --------------------------------------------------------------------------
+def rowsum(off, w):
+    off = np.asarray(off)
+    n = len(off) - 1
+    K = np.zeros(n, np.int64)
+    np.add.at(K, np.repeat(np.arange(n), np.diff(off)), np.asarray(w, np.int64))
+    return K
+
+
+def sigma_of(C, K, n):
+    s = np.zeros(n, np.int64)
+    np.add.at(s, C, K)
+    return s
+
+
+def phase_graphs():
+    yield "pp", S.planted_partition(600, 6, 0.08, 0.004, 11)
+    yield "rmat", S.rmat(9, 8, seed=5)
+    yield "er", S.erdos_renyi(120, 0.05, 9, wmax=3)
+    yield "grid", S.grid(20, 0.05, 0.01, seed=2)
+
+
+@pytest.mark.parametrize("name,g", list(phase_graphs()))
+@pytest.mark.parametrize("sched", [O.SCHED_DET, O.SCHED_GS])
+def test_phase_invariants_first_pass(name, g, sched):
+    off, idx, w = g
+    off, idx, w = np.asarray(off), np.asarray(idx), np.asarray(w, np.int64)
+    n = len(off) - 1
+    K = rowsum(off, w)
+    C = np.arange(n, dtype=np.int32)
+    Sg = K.copy()
+    ch = np.ones(n, np.uint8)
+    pr = np.zeros(n, np.uint8)
+    li, moves = O.local_move(off, idx, w, C, K, Sg, ch, pr, tau=0.01, sched=sched)
+    assert 1 <= li <= 20
+    assert np.array_equal(Sg, sigma_of(C, K, n))           # Sigma' = summed K'
+    # local-move leaves no improving single-vertex move when run to tau = 0
+    O.subset_renumber(C, Sg, ch)
+    for c in np.unique(C):                                   # label is the smallest member
+        assert c == np.flatnonzero(C == c).min()
+    assert np.array_equal(Sg, sigma_of(C, K, n))
+    CB = C.copy()
+    O.break_changed(C, K, Sg, ch)
+    assert np.array_equal(C, np.arange(n))
+    O.refine(off, idx, w, CB, C, K, Sg, ch, sched=sched)
+    assert np.array_equal(Sg, sigma_of(C, K, n))
+    for c in np.unique(C):                                   # refined inside one bound,
+        mem = np.flatnonzero(C == c)
+        assert len(np.unique(CB[mem])) == 1
+        assert B.components_within(off, idx, mem) == 1       # and connected
+    nc = O.renumber(C)
+    assert sorted(np.unique(C)) == list(range(nc))
+    off2, idx2, w2 = O.aggregate(off, idx, w, C, nc)
+    assert w2.sum() == w.sum()                               # 2m preserved
+    K2 = np.array([w2[off2[c]:off2[c + 1]].sum() for c in range(nc)])
+    assert np.array_equal(K2, sigma_of(C, K, nc))            # K'' = summed K'
+    q1, num1 = O.modularity(off, idx, w, C)
+    q2, num2 = O.modularity(off2, idx2, w2, np.arange(nc))
+    assert num1 == num2                                      # Q preserved exactly
+    # super-vertex graph is symmetric
+    A2 = {}
+    for c in range(nc):
+        for e in range(off2[c], off2[c + 1]):
+            A2[(c, int(idx2[e]))] = int(w2[e])
+    assert all(A2.get((b, a)) == v for (a, b), v in A2.items())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_local_move_to_tolerance_zero_leaves_no_improving_move(seed):
+    off, idx, w = rand_graph(12, 0.3, 300 + seed, wmax=3)
+    n = 12
+    K = np.array([w[off[i]:off[i + 1]].sum() for i in range(n)], np.int64)
+    for sched in (O.SCHED_DET, O.SCHED_GS):
+        C = np.arange(n, dtype=np.int32)
+        Sg = K.copy()
+        li, _ = O.local_move(off, idx, w, C, K, Sg, np.ones(n, np.uint8), np.zeros(n, np.uint8),
+                             tau=0.0, max_iters=1000, sched=sched)
+        if sched == O.SCHED_GS:
+            # sequential moves strictly raise Q, so GS must stop by itself
+            assert li < 1000
+        elif li == 1000:
+            # DET applies one colour class at once (Jacobi within the class) and
+            # may cycle on swaps; only its converged runs carry the guarantee
+            continue
+        A = B.dense(off, idx, w)
+        # moves into existing communities only: local-move never opens a new one
+        base = B.q_newman(A, C.tolist())
+        for i in range(n):
+            for c in set(C.tolist()):
+                if c != C[i]:
+                    D = C.tolist()
+                    D[i] = c
+                    assert B.q_newman(A, D) - base <= 0
+
+
+def test_subset_renumber_and_break_golden():
+    g = gold("subset_renumber.json")
+    C = np.array(g["C"], np.int32)
+    K = np.array(g["K"], np.int64)
+    Sg = np.array(g["Sigma"], np.int64)
+    ch = np.array(g["changed"], np.uint8)
+    O.subset_renumber(C, Sg, ch)
+    assert C.tolist() == g["after_renumber"]["C"]
+    assert Sg.tolist() == g["after_renumber"]["Sigma"]
+    assert ch.tolist() == g["after_renumber"]["changed"]
+    O.break_changed(C, K, Sg, ch)
+    assert C.tolist() == g["after_break"]["C"]
+    assert Sg.tolist() == g["after_break"]["Sigma"]
+
+
+def test_refinement_splits_disconnected_bound():
+    # bound {0..5} holds two triangles with no edge between them (Sec. 4.3,
+    # Fig. community-split): refinement must not keep them together.
+    us = [0, 0, 1, 3, 3, 4, 2, 5, 6, 7, 6]
+    vs = [1, 2, 2, 4, 5, 5, 6, 6, 7, 8, 8]
+    off, idx, w = S.edges_to_csr(9, us, vs)
+    w = w.astype(np.int64)
+    K = np.array([w[off[i]:off[i + 1]].sum() for i in range(9)], np.int64)
+    CB = np.array([0, 0, 0, 0, 0, 0, 6, 6, 6], np.int32)
+    for sched in (O.SCHED_DET, O.SCHED_GS):
+        C = np.arange(9, dtype=np.int32)
+        Sg = K.copy()
+        ch = np.zeros(9, np.uint8)
+        ch[0] = 1
+        O.refine(off, idx, w, CB, C, K, Sg, ch, sched=sched)
+        assert len(set(C[:3]) & set(C[3:6])) == 0
+        assert C[6:].tolist() == [6, 7, 8]                   # unchanged bound untouched
+        for c in np.unique(C):
+            assert B.components_within(off, idx, np.flatnonzero(C == c)) == 1
+
+
+# --------------------------------------------------------------------------
+# Dynamic front-ends
+# --------------------------------------------------------------------------
+def golden_batch():
+    g = gold("batch_marking.json")
+    n = g["n"]
+    e = np.array(g["edges_prev"])
+    off, idx, w = S.edges_to_csr(n, e[:, 0], e[:, 1])
+    d = np.array(g["dels"])
+    i = np.array(g["ins"])
+    dels = (d[:, 0], d[:, 1], d[:, 2])
+    ins = (i[:, 0], i[:, 1], i[:, 2])
+    return g, (off, idx, w), dels, ins
+
+
+def test_batch_golden_update_weights_and_marking():
+    g, (off, idx, w), dels, ins = golden_batch()
+    n = g["n"]
+    Cp = np.array(g["C_prev"], np.int32)
+    off_t, idx_t, w_t = O.apply_batch(off, idx, w, dels, ins)
+    Kt_rows = np.array([w_t[off_t[v]:off_t[v + 1]].sum() for v in range(n)])
+    assert Kt_rows.tolist() == g["K_t"]
+    assert int(w_t.sum()) == g["two_m_t"]
+    K = np.array([w[off[v]:off[v + 1]].sum() for v in range(n)], np.int64)
+    Sg = sigma_of(Cp, K, n)
+    O.update_weights(Cp, K, Sg, dels, ins)
+    assert K.tolist() == g["K_t"]
+    assert {str(c): int(Sg[c]) for c in np.unique(Cp)} == g["Sigma_t"]
+    ch = O.changed_communities(Cp, dels, ins)
+    assert np.flatnonzero(ch).tolist() == g["changed"]
+    assert np.flatnonzero(O.mark_df(Cp, dels, ins)).tolist() == g["df_affected"]
+    aff = O.mark_ds(off_t, idx_t, w_t, Cp, K, Sg, dels, ins)
+    assert np.flatnonzero(aff).tolist() == g["ds_affected"]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_update_weights_equals_recompute(seed):
+    off, idx, w = S.planted_partition(400, 4, 0.05, 0.005, 20 + seed)
+    n = 400
+    Cp = (np.arange(n) * 4 // n).astype(np.int32)
+    dels, ins = S.random_batch(off, idx, w, 60, seed)
+    off_t, idx_t, w_t = O.apply_batch(off, idx, w, dels, ins)
+    K = np.array([w[off[v]:off[v + 1]].sum() for v in range(n)], np.int64)
+    Sg = sigma_of(Cp, K, n)
+    O.update_weights(Cp, K, Sg, dels, ins)
+    Kt = np.array([w_t[off_t[v]:off_t[v + 1]].sum() for v in range(n)], np.int64)
+    assert np.array_equal(K, Kt)
+    assert np.array_equal(Sg, sigma_of(Cp, Kt, n))
+
+
+def test_apply_batch_roundtrip_and_symmetry():
+    off, idx, w = S.planted_partition(300, 3, 0.05, 0.005, 3)
+    dels, ins = S.random_batch(off, idx, w, 50, 7)
+    off_t, idx_t, w_t = O.apply_batch(off, idx, w, dels, ins)
+    # undo: delete what was inserted, insert what was deleted
+    off_b, idx_b, w_b = O.apply_batch(off_t, idx_t, w_t, ins, dels)
+    assert np.array_equal(off_b, off) and np.array_equal(idx_b, idx)
+    assert np.array_equal(w_b, w)
+    A = B.dense(off_t, idx_t, w_t)
+    assert all(A[i][j] == A[j][i] for i in range(300) for j in range(i))
+
+
+def test_apply_batch_rejects_bad_batches():
+    off, idx, w = S.ring_of_cliques(3, 3)
+    with pytest.raises(ValueError):
+        O.apply_batch(off, idx, w, ([0], [5], [1]), None)      # missing edge
+    with pytest.raises(ValueError):
+        O.apply_batch(off, idx, w, ([0], [1], [2]), None)      # weight mismatch
+    with pytest.raises(ValueError):
+        O.apply_batch(off, idx, w, None, ([2], [2], [1]))      # self-loop
+
+
+def converged_static(off, idx, w, opts):
+    """Static Leiden at tol = 0 whose last pass made no local move, so no
+    super-vertex move of its last level improves Q."""
+    res = O.static(off, idx, w, opts)
+    st = res.stats
+    last = st["passes"] - 1
+    assert st["iters"][last] == 1 and st["moves"][last] == 0 and st["ncomm"][last] == -1
+    return res.membership
+
+
+@pytest.mark.parametrize("g", [S.planted_partition(500, 5, 0.06, 0.004, 1),
+                               S.rmat(9, 8, seed=2), S.grid(15, 0.05, 0.01, seed=4)])
+@pytest.mark.parametrize("sched", [O.SCHED_DET, O.SCHED_GS])
+def test_empty_batch_leaves_converged_membership_unchanged(g, sched):
+    # With no update, DF and DS mark nothing, refine nothing, and the first
+    # pass only aggregates C^{t-1}; the next pass sees the converged last
+    # level of Static again and stops (Alg. leiden, Alg. frontier, Alg. delta).
+    off, idx, w = g
+    opts = O.LeidenOpts(tol=0.0, sched=sched, max_passes=30)
+    C = converged_static(off, idx, w, opts)
+    n = len(off) - 1
+    K = rowsum(off, w)
+    for mode in ("DS", "DF"):
+        r = O.update(off, idx, w, C, K, sigma_of(C, K, n), None, None, mode, opts)
+        assert np.array_equal(r.membership, C), mode
+        assert np.array_equal(r.Sigma, sigma_of(C, K, n))
+        assert r.stats["affected0"] == 0
+
+
+def test_nd_empty_batch_reaches_fixed_point():
+    # ND reprocesses every vertex; iterated on an empty batch it settles, and
+    # its fixed point has no improving single-vertex move (checked by brute
+    # force against Eq. 1).
+    off, idx, w = S.planted_partition(60, 3, 0.3, 0.03, 4)
+    n = 60
+    opts = O.LeidenOpts(tol=0.0, sched=O.SCHED_GS, max_passes=30)
+    C = O.static(off, idx, w, opts).membership
+    K = rowsum(off, w)
+    for _ in range(20):
+        r = O.update(off, idx, w, C, K, sigma_of(C, K, n), None, None, "ND", opts)
+        if np.array_equal(r.membership, C):
+            break
+        C = r.membership
+    else:
+        raise AssertionError("ND did not settle")
+    A = B.dense(off, idx, w)
+    assert B.max_single_move_gain(A, C.tolist()) <= 0
+
+
+def test_df_with_everything_affected_equals_static():
+    off, idx, w = S.planted_partition(800, 8, 0.05, 0.003, 5)
+    n = len(off) - 1
+    w64 = w.astype(np.int64)
+    K = np.array([w64[off[v]:off[v + 1]].sum() for v in range(n)], np.int64)
+    ident = np.arange(n, dtype=np.int32)
+    for sched in (O.SCHED_DET, O.SCHED_GS):
+        opts = O.LeidenOpts(sched=sched)
+        st = O.static(off, idx, w, opts)
+        raw, _ = O.leiden(off, idx, w, ident, K, K, np.ones(n, np.uint8), 0,
+                          np.ones(n, np.uint8), 1, opts)
+        assert np.array_equal(O.canonical(raw), st.membership)
+
+
+@pytest.mark.parametrize("mode", ["ND", "DS", "DF"])
+@pytest.mark.parametrize("sched", [O.SCHED_DET, O.SCHED_GS])
+def test_dynamic_update_invariants(mode, sched):
+    off, idx, w = S.planted_partition(1000, 10, 0.05, 0.002, 8)
+    n = 1000
+    opts = O.LeidenOpts(sched=sched)
+    st = O.static(off, idx, w, opts)
+    K = np.array([w[off[v]:off[v + 1]].sum() for v in range(n)], np.int64)
+    Sg = sigma_of(st.membership, K, n)
+    dels, ins = S.random_batch(off, idx, w, 40, 3)
+    off_t, idx_t, w_t = O.apply_batch(off, idx, w, dels, ins)
+    r = O.update(off_t, idx_t, w_t, st.membership, K, Sg, dels, ins, mode, opts)
+    Kt = np.array([w_t[off_t[v]:off_t[v + 1]].sum() for v in range(n)], np.int64)
+    assert np.array_equal(r.K, Kt)
+    assert np.array_equal(r.Sigma, sigma_of(r.membership, Kt, n))
+    assert np.array_equal(r.membership, O.canonical(r.membership))
+    assert B.all_connected(off_t, idx_t, r.membership)
+    # Sec. 5.2: dynamic modularity is no worse than Static on the same G^t
+    # beyond a small margin (it is often better: it starts from C^{t-1})
+    st_t = O.static(off_t, idx_t, w_t, opts)
+    assert r.q >= st_t.q - 0.02
+    # without K/Sigma the oracle recomputes them: same answer
+    r2 = O.update(off_t, idx_t, w_t, st.membership, None, None, dels, ins, mode, opts)
+    assert np.array_equal(r2.membership, r.membership)
+
+
+def test_df_marks_no_more_than_ds():
+    # Sec. 5.3: DF marks fewer affected vertices than DS
+    off, idx, w = S.planted_partition(2000, 10, 0.03, 0.002, 12)
+    n = 2000
+    st = O.static(off, idx, w)
+    K = np.array([w[off[v]:off[v + 1]].sum() for v in range(n)], np.int64)
+    Sg = sigma_of(st.membership, K, n)
+    dels, ins = S.random_batch(off, idx, w, 20, 1)
+    off_t, idx_t, w_t = O.apply_batch(off, idx, w, dels, ins)
+    Kt, St = K.copy(), Sg.copy()
+    O.update_weights(st.membership, Kt, St, dels, ins)
+    df = O.mark_df(st.membership, dels, ins)
+    ds = O.mark_ds(off_t, idx_t, w_t, st.membership, Kt, St, dels, ins)
+    assert df.sum() <= ds.sum()
+    assert np.all(ds[df.astype(bool)] == 1)
+
+
+def test_det_class_partition():
+    for S_ in (1, 2, 8, 64):
+        cls = [O.det_class(i, S_) for i in range(5000)]
+        assert min(cls) == 0 and max(cls) == S_ - 1
+        if S_ > 1:
+            counts = np.bincount(cls, minlength=S_)
+            assert counts.min() > 5000 / S_ * 0.7
+        for i in (0, 1, 12345, 2**31 - 1):
+            h = (i * 2654435761) % 2**32
+            assert O.det_class(i, S_) == (h >> (32 - int(np.log2(S_))) if S_ > 1 else 0)
+
+
+def test_degenerate_graphs():
+    # no vertices, no edges, isolated vertices, a single edge
+    for off, idx, w in [
+        (np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32)),
+        (np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32)),
+        S.edges_to_csr(4, [0], [1]),
+    ]:
+        res = O.static(off, idx, w)
+        n = len(off) - 1
+        assert len(res.membership) == n
+        assert np.array_equal(res.membership, O.canonical(res.membership))
+        if n == 4:
+            assert res.membership.tolist() == [0, 0, 1, 2]
+        else:
+            assert res.membership.tolist() == list(range(n))
+            assert res.q == 0.0
