@@ -1,0 +1,354 @@
+"""Benchmark: Static and Dynamic Frontier Leiden on an R-MAT scale-22 graph.
+
+Workload (one GPU): R-MAT scale 22, edge factor 16, (a, b, c, d) = (0.57,
+0.19, 0.19, 0.05), symmetrised, deduplicated, self-loops dropped, unit int32
+weights (4.19M vertices, ~1.3e8 CSR entries, ~1.1 GB of CSR: larger than the
+129 MB L2, so no flush is needed between steps).  Random batches of 1e-5,
+1e-4 and 1e-3 |E| undirected updates (80% insertions between uniform vertex
+pairs, 20% deletions of uniform existing edges, unit weight), each applied to
+the base graph separately (Sec. 5.1.4).
+
+One step, all on the device: apply the step's batch to the base graph (a1),
+DF update from the base graph's membership (a2..a10), then Static Leiden on
+the same updated graph (a4..a10).  The headline value is Static Leiden's CSR
+entries processed per second per pass, sum_p nnz(G'_p) / t_static; the DF
+update time is reported beside it (p50 / p99 per batch size, and the speedup
+over Static on the same G^t).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (its own seed): the
+method has no data-path exchange, so scaling is weak and there is no
+collective beyond the timing barrier.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges/s per Leiden pass; DF batch update time & p50/p99 vs GPU Static, same GPU"
+SCALE, EDGE_FACTOR = 22, 16
+BATCH_FRACS = (1e-5, 1e-4, 1e-3)
+GRAPH_SEED = 0x1EDE0 + 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=9)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=SCALE)
+    ap.add_argument("--sched", default="det", choices=["det", "async"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001 -- the file is written by the driver
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(scale, seed, nsteps):
+    from paper_2405_11658_gb300 import synth as S
+    g = S.rmat(scale, EDGE_FACTOR, 0.57, 0.19, 0.19, seed=seed)
+    nedges = len(g[1]) // 2
+    pairs = S.undirected_pairs(*g) if nsteps else None
+    batches = []
+    for k in range(nsteps):
+        frac = BATCH_FRACS[k % len(BATCH_FRACS)]
+        size = max(2, int(round(frac * nedges)))
+        batches.append((frac, S.random_batch(*g, size, seed=1000 + k, pairs=pairs)))
+    return g, batches
+
+
+def cpu_baseline(g, max_passes=1):
+    """The oracle as it stands, single-threaded, on the first pass of Static
+    Leiden over the same graph: CSR entries per second of that pass."""
+    import oracle as O
+    t0 = time.perf_counter()
+    r = O.static(*g, O.LeidenOpts(max_passes=max_passes))
+    wall = time.perf_counter() - t0
+    st = r.stats
+    edges = sum(st["nnz"][:st["passes"]])
+    secs = sum(st["t_pass"][:st["passes"]])
+    return {"value": edges / secs, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {max_passes} pass(es) of Static Leiden (DET) on the same R-MAT graph, "
+                      f"{st['nnz'][0]} CSR entries; {wall:.1f} s of CPU work",
+            "seconds": round(wall, 3)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    g, _ = make_inputs(args.scale, GRAPH_SEED, 0)
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(g))
+    total = time.perf_counter() - t0
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": f"rmat-s{args.scale}-ef{EDGE_FACTOR} static leiden, first pass",
+                       "graph": f"R-MAT scale {args.scale}, edge factor {EDGE_FACTOR}"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[0]["sample"], "value": v,
+                             "unit": "edges/s"},
+            "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2405_11658_gb300 as L
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nsteps = args.warmup + args.steps
+    g, batches = make_inputs(args.scale, GRAPH_SEED + 7919 * rank, nsteps)
+    off, idx, w = g
+    n, nnz = len(off) - 1, len(idx)
+    max_nnz = nnz + 2 * max(len(b[1][0]) for _, b in batches) + 16
+    stream = torch.cuda.current_stream()
+    opts = L.Opts(sched=L.DET if args.sched == "det" else L.ASYNC)
+    G0 = L.Graph.from_numpy(off, idx, w, device=dev)
+    dev_batches = [(f, L.Edges.from_numpy(d, device=dev), L.Edges.from_numpy(i, device=dev))
+                   for f, (d, i) in batches]
+    ctx = L.Context(max_n=n, max_nnz=max_nnz, stream=stream)
+    Cs, _ = ctx.static(G0, opts, want_q=False)
+    # base membership with consistent auxiliary information (K, Sigma): one
+    # ND pass over the unchanged graph returns C0 together with K0 and S0
+    C0, K0, S0, _ = ctx.update(G0, Cs, None, None, "ND", opts, want_q=False)
+
+    rec = []
+
+    def step(k, timed):
+        frac, dE, iE = dev_batches[k]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        Gt = ctx.apply_batch(G0, dE, iE, cap_nnz=max_nnz)
+        ev[1].record(stream)
+        memb, _, _, qdf = ctx.update(Gt, C0, dE, iE, "DF", opts, prior_K=K0, prior_Sigma=S0, want_q=False)
+        ev[2].record(stream)
+        if timed:
+            ctx.set_timing(True)
+        ms, _ = ctx.static(Gt, opts, want_q=False)
+        ev[3].record(stream)
+        if timed:
+            ctx.set_timing(False)
+        st = ctx.stats()
+        torch.cuda.synchronize()
+        t = [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+        rec.append({"frac": frac, "apply_ms": t[0], "df_ms": t[1], "static_ms": t[2],
+                    "static_edges": sum(st["nnz"][:st["passes"]]), "stats": st})
+
+    for k in range(args.warmup):
+        step(k, False)
+    rec.clear()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        e_start = torch.cuda.Event(enable_timing=True)
+        e_end = torch.cuda.Event(enable_timing=True)
+        e_start.record(stream)
+        for k in range(args.warmup, nsteps):
+            step(k, True)
+        e_end.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    total_ms = e_start.elapsed_time(e_end)
+    static_ms = sum(r["static_ms"] for r in rec)
+    static_edges = sum(r["static_edges"] for r in rec)
+    # max over ranks of the device time
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, static_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([static_edges], device=dev, dtype=torch.float64)
+        dist.all_reduce(e)
+        total_ms, static_ms = float(t[0]), float(t[1])
+        static_edges_all = float(e[0])
+    else:
+        static_edges_all = static_edges
+    value = static_edges_all / (static_ms / 1000.0)
+
+    # roofline of the dominant kernel family (local-move decide kernels)
+    mv_bytes = sum(r["stats"]["move_bytes"] for r in rec)
+    mv_ms = sum(r["stats"]["move_kernel_ms"] for r in rec)
+    mv_launches = sum(r["stats"]["move_kernel_launches"] for r in rec)
+    peak, peak_kind = peaks()
+    achieved = (mv_bytes / mv_launches) / ((mv_ms / mv_launches) / 1000.0) / 1e9 if mv_ms > 0 else None
+
+    # DF vs Static per batch size
+    df = {}
+    for frac in BATCH_FRACS:
+        rs = [r for r in rec if r["frac"] == frac]
+        if not rs:
+            continue
+        d = sorted(r["df_ms"] for r in rs)
+        s = sorted(r["static_ms"] for r in rs)
+        df[f"{frac:g}"] = {"df_ms_p50": float(np.percentile(d, 50)), "df_ms_p99": float(np.percentile(d, 99)),
+                           "static_ms_p50": float(np.percentile(s, 50)),
+                           "speedup_vs_static": float(np.median(s) / np.median(d)),
+                           "apply_ms_p50": float(np.median([r["apply_ms"] for r in rs])), "samples": len(rs)}
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        off_h = torch.from_numpy(off).pin_memory()
+        idx_h = torch.from_numpy(idx).pin_memory()
+        w_h = torch.from_numpy(w).pin_memory()
+        m_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        Gd = L.Graph(torch.empty_like(off_h, device=dev), torch.empty_like(idx_h, device=dev),
+                     torch.empty_like(w_h, device=dev))
+        mdev = torch.empty(n, dtype=torch.int32, device=dev)
+        e_edges, e_ms = 0, 0.0
+        for k in range(args.e2e_steps + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            Gd.off.copy_(off_h, non_blocking=True)
+            Gd.idx.copy_(idx_h, non_blocking=True)
+            Gd.w.copy_(w_h, non_blocking=True)
+            ctx.static(Gd, opts, out=mdev, want_q=False)
+            m_h.copy_(mdev, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            if k > 0:  # the first round is a warm-up
+                e_edges += sum(st["nnz"][:st["passes"]])
+                e_ms += a.elapsed_time(b)
+        e2e = {"value": e_edges / (e_ms / 1000.0), "unit": "edges/s",
+               "h2d_bytes_per_step": int(off.nbytes + idx.nbytes + w.nbytes), "d2h_bytes_per_step": int(n * 4)}
+
+    base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        base = cpu_baseline(g)
+
+    ctx.close()
+    if rank == 0:
+        last = rec[-1]["stats"] if rec else {}
+        line = {
+            "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"rmat-s{args.scale}-ef{EDGE_FACTOR}: batch apply + DF update + Static Leiden",
+                       "graph": f"R-MAT scale {args.scale}, edge factor {EDGE_FACTOR}, a/b/c/d=0.57/0.19/0.19/0.05",
+                       "vertices": n, "csr_entries": nnz, "batch_fracs": list(BATCH_FRACS),
+                       "schedule": args.sched, "l2": "inputs larger than L2 (CSR 1.1 GB), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "static_ms_mean": static_ms / max(1, len(rec)),
+            "static_passes": last.get("passes"), "static_iters": last.get("iters"),
+            "df": df,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "local-move decide (all degree tiers)", "peak_kind": peak_kind,
+                         "bytes_per_launch": mv_bytes / max(1, mv_launches),
+                         "ms_per_launch": mv_ms / max(1, mv_launches), "launches": mv_launches},
+            "cpu_baseline": base,
+            "e2e": e2e,
+            "gpu_launches": None,
+            "clocks": clk.summary(),
+            "wall_s": wall,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

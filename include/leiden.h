@@ -1,0 +1,187 @@
+/*
+ * leiden.h -- C-ABI of the GB300 (sm_103a) library for Static, Naive-dynamic
+ * (ND), Delta-screening (DS) and Dynamic Frontier (DF) Leiden community
+ * detection (arXiv 2405.11658).
+ *
+ * Problem statement (Sec. 3.5, Sec. 4.5, Appendix A): Static Leiden maps a
+ * graph G to a community membership C; a dynamic update takes the updated
+ * snapshot G^t, the batch of edge deletions D- and insertions D+ that produced
+ * it, the previous membership C^{t-1}, weighted degrees K^{t-1} and community
+ * totals Sigma^{t-1}, and returns C^t, K^t and Sigma^t.
+ *
+ * General conventions
+ *   - All graph, batch and output arrays are DEVICE pointers owned by the
+ *     caller, unless a field says HOST.  The library never frees them.
+ *   - A graph is a symmetric CSR without duplicate entries: off[n+1] (int64,
+ *     off[0] = 0), idx[nnz] (int32 column IDs in [0, n)), w[nnz] (int32, > 0).
+ *     A self-loop (i,i,w) is stored once and adds w to K_i and to 2m (Sec. 3
+ *     definitions of K_i and m).  Rows need not be sorted, except for
+ *     leiden_apply_batch (below).
+ *   - A batch lists each undirected pair once, (src, dst, w); the library
+ *     applies both directions, as every update carries its reverse edge
+ *     (Sec. 5.1.4).  Self-loops are rejected.
+ *   - Membership outputs are canonical: the community holding the smallest
+ *     vertex is 0, the next smallest unseen vertex opens community 1, and so on.
+ *   - Every call is ordered on the context's CUDA stream.  Calls that return a
+ *     host scalar (q_out, nnz_out) or read sizes back synchronise that stream.
+ *   - Return value: LEIDEN_OK (0) or a negative LEIDEN_E* code.  On error,
+ *     outputs are unspecified (the library may have written part of them);
+ *     the context stays usable unless the code is LEIDEN_ECUDA.
+ *   - Integer arithmetic is exact: K and Sigma in int64, the delta-modularity
+ *     of Eq. 2 scaled by 2m^2 q in 128-bit integers.  The resolution gamma
+ *     must be an exact multiple of 2^-20 (gamma = p/q, q = 2^20), else
+ *     LEIDEN_EINVAL.  2m must stay below 2^40 (else LEIDEN_EOVERFLOW).
+ */
+#ifndef LEIDEN_H
+#define LEIDEN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LEIDEN_OK 0
+#define LEIDEN_EINVAL (-1)     /* bad argument, bad ID, bad batch, bad gamma */
+#define LEIDEN_ENOMEM (-2)     /* a size exceeds the context's capacity, or allocation failed */
+#define LEIDEN_EOVERFLOW (-3)  /* 2m >= 2^40 */
+#define LEIDEN_ETIMEOUT (-4)   /* a bounded device wait expired */
+#define LEIDEN_ECUDA (-5)      /* a CUDA call failed; the context should be destroyed */
+
+typedef struct {
+  int64_t n;            /* vertices, 0 <= n < 2^31 */
+  int64_t nnz;          /* CSR entries (= off[n]) */
+  const int64_t *off;   /* DEVICE [n+1] */
+  const int32_t *idx;   /* DEVICE [nnz] */
+  const int32_t *w;     /* DEVICE [nnz], > 0 */
+} leiden_csr;
+
+typedef struct {
+  int64_t count;        /* undirected pairs */
+  const int32_t *src;   /* DEVICE [count] */
+  const int32_t *dst;   /* DEVICE [count] */
+  const int32_t *w;     /* DEVICE [count], > 0; for a deletion, the weight of the deleted edge */
+} leiden_edges;
+
+enum { LEIDEN_ND = 1, LEIDEN_DS = 2, LEIDEN_DF = 3 };
+
+/* Schedules.  DET: every local-move iteration (and the refinement sweep) runs
+ * det_subsets sub-sweeps over colour classes (class(i) = top log2(S) bits of
+ * (uint32)(i * 2654435761)); the moves of a sub-sweep are chosen against the
+ * state at its start and applied together, so the result does not depend on
+ * thread timing.  ASYNC: vertices move in place as soon as they decide, as in
+ * the paper's asynchronous CPU implementation (Sec. 4.7); results vary with
+ * timing. */
+enum { LEIDEN_DET = 0, LEIDEN_ASYNC = 1 };
+
+typedef struct {
+  double gamma;                  /* resolution (1.0) */
+  double tol;                    /* initial iteration tolerance tau (0.01, Sec. 4.7) */
+  double tol_drop;               /* tau divisor per pass (10, Sec. 4.7) */
+  int32_t max_iters;             /* MAX_ITERATIONS per local-moving phase (20, Sec. 4.7) */
+  int32_t max_passes;            /* MAX_PASSES (10; not stated by the paper) */
+  int32_t sched;                 /* LEIDEN_DET or LEIDEN_ASYNC */
+  int32_t det_subsets;           /* DET colour classes: power of two in [1, 256] (8) */
+  int32_t refine_all_first_pass; /* Full Refine variant (Sec. 4.2): refine every community in pass 0 */
+  int32_t reserved[3];           /* must be 0 */
+} leiden_opts;
+
+/* Fills the defaults listed above. */
+void leiden_opts_default(leiden_opts *opts);
+
+typedef struct leiden_ctx leiden_ctx;
+
+/* Creates a context bound to one CUDA stream (cudaStream_t passed as void*;
+ * NULL = the legacy default stream) on the current device, and allocates its
+ * device workspace for graphs of up to max_n vertices and max_nnz CSR entries
+ * (about 100 B per vertex plus 52 B per entry).  The stream is borrowed and
+ * must outlive the context.  Errors: LEIDEN_EINVAL (sizes out of range),
+ * LEIDEN_ENOMEM, LEIDEN_ECUDA. */
+int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_t max_nnz);
+
+/* Synchronises the stream and frees the workspace.  NULL is a no-op. */
+void leiden_ctx_destroy(leiden_ctx *ctx);
+
+/* Static Leiden (Alg. leiden with every vertex affected and every community
+ * changed, Sec. 4.6): membership_out DEVICE [n] receives canonical labels;
+ * q_out (HOST, may be NULL) receives the modularity of Eq. 1 at resolution
+ * gamma.  Errors: LEIDEN_EINVAL, LEIDEN_ENOMEM (n or nnz above the context's
+ * capacity), LEIDEN_EOVERFLOW, LEIDEN_ECUDA. */
+int leiden_static(leiden_ctx *ctx, const leiden_csr *g, const leiden_opts *opts,
+                  int32_t *membership_out, double *q_out);
+
+/* ND / DS / DF update (Alg. naive, Alg. delta, Alg. frontier with
+ * Alg. update and Alg. leiden).  g_t is the updated snapshot G^t, already
+ * containing the batch (see leiden_apply_batch); del / ins is the batch that
+ * produced it (either may be NULL or empty).  prior_membership DEVICE [n]
+ * holds C^{t-1} (any labels in [0, n)); prior_K and prior_Sigma DEVICE [n]
+ * hold K^{t-1} and Sigma^{t-1} indexed by those labels, or are both NULL, in
+ * which case K^t and Sigma^t are recomputed from G^t.  Outputs (DEVICE [n]):
+ * canonical C^t, K^t, and Sigma^t indexed by the canonical labels of C^t
+ * (zero beyond the last community); K_out, Sigma_out and q_out may be NULL.
+ * mode: LEIDEN_ND, LEIDEN_DS or LEIDEN_DF.  Errors as leiden_static, plus
+ * LEIDEN_EINVAL for a bad mode or batch IDs outside [0, n). */
+int leiden_update(leiden_ctx *ctx, const leiden_csr *g_t,
+                  const int32_t *prior_membership, const int64_t *prior_K,
+                  const int64_t *prior_Sigma, const leiden_edges *del,
+                  const leiden_edges *ins, int32_t mode, const leiden_opts *opts,
+                  int32_t *membership_out, int64_t *K_out, int64_t *Sigma_out,
+                  double *q_out);
+
+/* Modularity (Eq. 1 at resolution gamma) of membership (DEVICE [n], labels
+ * in [0, n)) on g.  q_out is HOST.  Errors: LEIDEN_EINVAL, LEIDEN_ENOMEM,
+ * LEIDEN_ECUDA. */
+int leiden_modularity(leiden_ctx *ctx, const leiden_csr *g, const int32_t *membership,
+                      double gamma, double *q_out);
+
+/* Builds G^t = G^{t-1} - D- + D+ (Sec. 3.5) on the device.  g_prev must have
+ * sorted rows; the output rows are sorted.  A deletion removes the edge
+ * {src, dst}; it must exist with weight w.  Deletions apply before insertions;
+ * an insertion of an existing (or repeated) pair adds its weight.  off_out
+ * DEVICE [n+1], idx_out / w_out DEVICE [cap_nnz]; nnz_out (HOST) receives the
+ * new entry count.  Errors: LEIDEN_EINVAL (bad IDs, self-loop, missing edge
+ * or weight mismatch on deletion, duplicate deletion, unsorted rows),
+ * LEIDEN_ENOMEM (result larger than cap_nnz or the context), LEIDEN_ECUDA. */
+int leiden_apply_batch(leiden_ctx *ctx, const leiden_csr *g_prev, const leiden_edges *del,
+                       const leiden_edges *ins, int64_t *off_out, int32_t *idx_out,
+                       int32_t *w_out, int64_t cap_nnz, int64_t *nnz_out);
+
+/* Per-call statistics of the last leiden_static / leiden_update call. */
+#define LEIDEN_STATS_PASSES 32
+typedef struct {
+  int32_t passes;                               /* passes started */
+  int32_t iters[LEIDEN_STATS_PASSES];           /* l_i of each local-moving phase */
+  int64_t nv[LEIDEN_STATS_PASSES];              /* |V'| at each pass */
+  int64_t nnz[LEIDEN_STATS_PASSES];             /* CSR entries of G' at each pass */
+  int64_t moves[LEIDEN_STATS_PASSES];           /* local-move migrations */
+  int64_t refine_moves[LEIDEN_STATS_PASSES];
+  int64_t affected0;                            /* vertices unprocessed at the start */
+  int64_t changed0;                             /* communities flagged changed before the first refinement */
+  /* device time of the local-move decide kernels, measured with CUDA events on
+   * the context stream when timing is enabled (leiden_ctx_set_timing) */
+  double move_kernel_ms;
+  int64_t move_kernel_launches;
+  int64_t move_scanned_entries;                 /* CSR entries the decide kernels read */
+  int64_t move_scanned_vertices;
+  double move_bytes;                            /* algorithmic bytes of those launches */
+  double total_ms;                              /* host wall time of the call */
+} leiden_run_stats;
+
+/* Copies the statistics of the last run into *out (HOST). */
+int leiden_get_stats(leiden_ctx *ctx, leiden_run_stats *out);
+
+/* Enables (1) or disables (0) CUDA-event timing of the local-move kernels. */
+int leiden_ctx_set_timing(leiden_ctx *ctx, int32_t enable);
+
+/* Detail of the context's last failure (a CUDA error name and message, or a
+ * device consistency check), empty if none; owned by the context and valid
+ * until its next call. */
+const char *leiden_ctx_last_error(leiden_ctx *ctx);
+
+/* Human-readable name of an error code (static storage). */
+const char *leiden_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

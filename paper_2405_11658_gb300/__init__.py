@@ -1,0 +1,308 @@
+"""Python binding of ``libleiden`` -- GB300 (sm_103a) Static / ND / DS / DF
+Leiden community detection (arXiv 2405.11658).
+
+This module only marshals arguments to the C-ABI declared in
+``include/leiden.h``: every step of the method runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the CUDA stream.  There is no CPU
+fallback: if ``libleiden.so`` is missing or fails to load, every call raises.
+
+Typical use::
+
+    import torch, paper_2405_11658_gb300 as L
+    g = L.Graph.from_numpy(off, idx, w)            # device-resident CSR
+    with L.Context(max_n=g.n, max_nnz=g.nnz) as ctx:
+        memb, q = ctx.static(g)                     # canonical labels, Eq. 1
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libleiden.so")
+
+LEIDEN_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EOVERFLOW", -4: "ETIMEOUT", -5: "ECUDA"}
+ND, DS, DF = 1, 2, 3
+MODES = {"ND": ND, "DS": DS, "DF": DF}
+DET, ASYNC = 0, 1
+STATS_PASSES = 32
+
+
+class LeidenError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str = ""):
+        self.code = code
+        self.detail = detail
+        extra = f"; {detail}" if detail else ""
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({_strerror(code)}){extra}")
+
+
+class _Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("off", C.c_void_p),
+                ("idx", C.c_void_p), ("w", C.c_void_p)]
+
+
+class _Edges(C.Structure):
+    _fields_ = [("count", C.c_int64), ("src", C.c_void_p), ("dst", C.c_void_p),
+                ("w", C.c_void_p)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("tol", C.c_double), ("tol_drop", C.c_double),
+                ("max_iters", C.c_int32), ("max_passes", C.c_int32), ("sched", C.c_int32),
+                ("det_subsets", C.c_int32), ("refine_all_first_pass", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("passes", C.c_int32),
+                ("iters", C.c_int32 * STATS_PASSES),
+                ("nv", C.c_int64 * STATS_PASSES),
+                ("nnz", C.c_int64 * STATS_PASSES),
+                ("moves", C.c_int64 * STATS_PASSES),
+                ("refine_moves", C.c_int64 * STATS_PASSES),
+                ("affected0", C.c_int64), ("changed0", C.c_int64),
+                ("move_kernel_ms", C.c_double), ("move_kernel_launches", C.c_int64),
+                ("move_scanned_entries", C.c_int64), ("move_scanned_vertices", C.c_int64),
+                ("move_bytes", C.c_double), ("total_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        k = min(self.passes, STATS_PASSES)
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        for name in ("iters", "nv", "nnz", "moves", "refine_moves"):
+            d[name] = list(getattr(self, name))[:k]
+        return d
+
+
+_lib = None
+
+
+def lib():
+    """Loads libleiden.so (building it first when nvcc is available)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        from . import build as _build
+        _build.build()
+    L = C.CDLL(LIB_PATH)
+    P, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    L.leiden_opts_default.argtypes = [P]
+    L.leiden_opts_default.restype = None
+    L.leiden_strerror.argtypes = [C.c_int]
+    L.leiden_strerror.restype = C.c_char_p
+    L.leiden_ctx_create.argtypes = [P, P, i64, i64]
+    L.leiden_ctx_create.restype = C.c_int
+    L.leiden_ctx_destroy.argtypes = [P]
+    L.leiden_ctx_destroy.restype = None
+    L.leiden_ctx_set_timing.argtypes = [P, i32]
+    L.leiden_ctx_set_timing.restype = C.c_int
+    L.leiden_ctx_last_error.argtypes = [P]
+    L.leiden_ctx_last_error.restype = C.c_char_p
+    L.leiden_get_stats.argtypes = [P, P]
+    L.leiden_get_stats.restype = C.c_int
+    L.leiden_static.argtypes = [P, P, P, P, P]
+    L.leiden_static.restype = C.c_int
+    L.leiden_update.argtypes = [P, P, P, P, P, P, P, i32, P, P, P, P, P]
+    L.leiden_update.restype = C.c_int
+    L.leiden_modularity.argtypes = [P, P, P, d, P]
+    L.leiden_modularity.restype = C.c_int
+    L.leiden_apply_batch.argtypes = [P, P, P, P, P, P, P, i64, P]
+    L.leiden_apply_batch.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _strerror(code: int) -> str:
+    try:
+        return lib().leiden_strerror(code).decode()
+    except Exception:  # noqa: BLE001 -- used while formatting another error
+        return "?"
+
+
+def _check(rc: int, what: str, ctx=None):
+    if rc != LEIDEN_OK:
+        detail = ""
+        if ctx:
+            try:
+                detail = (lib().leiden_ctx_last_error(ctx) or b"").decode()
+            except Exception:  # noqa: BLE001
+                detail = ""
+        raise LeidenError(rc, what, detail)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev(a, dtype, device):
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=dtype).contiguous()
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dtype)
+
+
+@dataclass
+class Opts:
+    gamma: float = 1.0
+    tol: float = 1e-2
+    tol_drop: float = 10.0
+    max_iters: int = 20
+    max_passes: int = 10
+    sched: int = DET
+    det_subsets: int = 8
+    refine_all_first_pass: int = 0
+
+    def c(self) -> _Opts:
+        o = _Opts()
+        o.gamma, o.tol, o.tol_drop = self.gamma, self.tol, self.tol_drop
+        o.max_iters, o.max_passes, o.sched = self.max_iters, self.max_passes, self.sched
+        o.det_subsets, o.refine_all_first_pass = self.det_subsets, self.refine_all_first_pass
+        return o
+
+
+class Graph:
+    """Symmetric CSR held in device tensors (int64 off, int32 idx, int32 w)."""
+
+    def __init__(self, off, idx, w):
+        self.off, self.idx, self.w = off, idx, w
+        self.n = int(off.numel()) - 1
+        self.nnz = int(idx.numel())
+
+    @classmethod
+    def from_numpy(cls, off, idx, w, device="cuda"):
+        torch = _torch()
+        return cls(_dev(off, torch.int64, device), _dev(idx, torch.int32, device),
+                   _dev(w, torch.int32, device))
+
+    def c(self) -> _Csr:
+        return _Csr(self.n, self.nnz, _ptr(self.off), _ptr(self.idx), _ptr(self.w))
+
+
+class Edges:
+    """A batch of undirected pairs (src, dst, w) in device tensors."""
+
+    def __init__(self, src, dst, w):
+        self.src, self.dst, self.w = src, dst, w
+        self.count = int(src.numel())
+
+    @classmethod
+    def from_numpy(cls, triple, device="cuda"):
+        torch = _torch()
+        s, d, w = triple
+        return cls(_dev(s, torch.int32, device), _dev(d, torch.int32, device),
+                   _dev(w, torch.int32, device))
+
+    def c(self) -> _Edges:
+        return _Edges(self.count, _ptr(self.src), _ptr(self.dst), _ptr(self.w))
+
+
+class Context:
+    """A ``leiden_ctx``: device workspace for graphs up to (max_n, max_nnz),
+    bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, max_n: int, max_nnz: int, stream=None):
+        torch = _torch()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = C.c_void_p()
+        _check(lib().leiden_ctx_create(C.byref(self._h), C.c_void_p(self.stream.cuda_stream),
+                                       int(max_n), int(max_nnz)), "leiden_ctx_create")
+        self.max_n, self.max_nnz = max_n, max_nnz
+
+    def close(self):
+        if self._h:
+            lib().leiden_ctx_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def set_timing(self, on: bool):
+        _check(lib().leiden_ctx_set_timing(self._h, 1 if on else 0), "leiden_ctx_set_timing")
+
+    def stats(self) -> dict:
+        st = _Stats()
+        _check(lib().leiden_get_stats(self._h, C.byref(st)), "leiden_get_stats")
+        return st.as_dict()
+
+    def static(self, g: Graph, opts: Opts | None = None, out=None, want_q: bool = True):
+        torch = _torch()
+        opts = opts or Opts()
+        memb = out if out is not None else torch.empty(g.n, dtype=torch.int32, device=g.off.device)
+        q = C.c_double()
+        gc, oc = g.c(), opts.c()
+        _check(lib().leiden_static(self._h, C.byref(gc), C.byref(oc), _ptr(memb),
+                                   C.byref(q) if want_q else None), "leiden_static", self._h)
+        return memb, (q.value if want_q else None)
+
+    def update(self, g: Graph, prior, dels: Edges | None, ins: Edges | None, mode: str,
+               opts: Opts | None = None, prior_K=None, prior_Sigma=None, want_q: bool = True,
+               out=None, K_out=None, Sigma_out=None):
+        torch = _torch()
+        opts = opts or Opts()
+        dev = g.off.device
+        memb = out if out is not None else torch.empty(g.n, dtype=torch.int32, device=dev)
+        K = K_out if K_out is not None else torch.empty(g.n, dtype=torch.int64, device=dev)
+        S = Sigma_out if Sigma_out is not None else torch.empty(g.n, dtype=torch.int64, device=dev)
+        q = C.c_double()
+        gc, oc = g.c(), opts.c()
+        dc = dels.c() if dels is not None else None
+        ic = ins.c() if ins is not None else None
+        _check(lib().leiden_update(self._h, C.byref(gc), _ptr(prior), _ptr(prior_K), _ptr(prior_Sigma),
+                                   C.byref(dc) if dc is not None else None,
+                                   C.byref(ic) if ic is not None else None,
+                                   MODES[mode] if isinstance(mode, str) else int(mode), C.byref(oc),
+                                   _ptr(memb), _ptr(K), _ptr(S), C.byref(q) if want_q else None),
+               "leiden_update", self._h)
+        return memb, K, S, (q.value if want_q else None)
+
+    def modularity(self, g: Graph, memb, gamma: float = 1.0) -> float:
+        q = C.c_double()
+        gc = g.c()
+        _check(lib().leiden_modularity(self._h, C.byref(gc), _ptr(memb), gamma, C.byref(q)),
+               "leiden_modularity", self._h)
+        return q.value
+
+    def apply_batch(self, g: Graph, dels: Edges | None, ins: Edges | None, cap_nnz: int | None = None):
+        torch = _torch()
+        dev = g.off.device
+        if cap_nnz is None:
+            cap_nnz = g.nnz + 2 * (ins.count if ins is not None else 0)
+        off = torch.empty(g.n + 1, dtype=torch.int64, device=dev)
+        idx = torch.empty(max(cap_nnz, 1), dtype=torch.int32, device=dev)
+        w = torch.empty(max(cap_nnz, 1), dtype=torch.int32, device=dev)
+        nnz = C.c_int64()
+        gc = g.c()
+        dc = dels.c() if dels is not None else None
+        ic = ins.c() if ins is not None else None
+        _check(lib().leiden_apply_batch(self._h, C.byref(gc), C.byref(dc) if dc is not None else None,
+                                        C.byref(ic) if ic is not None else None, _ptr(off), _ptr(idx),
+                                        _ptr(w), int(cap_nnz), C.byref(nnz)), "leiden_apply_batch", self._h)
+        return Graph(off, idx[:nnz.value], w[:nnz.value])
+
+
+def default_opts() -> dict:
+    o = _Opts()
+    lib().leiden_opts_default(C.byref(o))
+    return {name: getattr(o, name) for name, _ in o._fields_ if name != "reserved"}
+
+
+EXPORTED = ("leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
+            "leiden_update", "leiden_modularity", "leiden_apply_batch", "leiden_get_stats",
+            "leiden_ctx_set_timing", "leiden_strerror")

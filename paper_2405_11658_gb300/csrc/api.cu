@@ -1,0 +1,831 @@
+// api.cu -- C-ABI entry points and the host driver of the pass loop
+// (Alg. leiden) for Static, ND, DS and DF Leiden on one GPU.
+//
+// The driver keeps every array of the current super-vertex graph resident in
+// the context's workspace; it synchronises the stream once per local-moving
+// iteration (to test the iteration's total delta-modularity against tau) and
+// once per pass (to read the community count after renumbering).
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "leiden.h"
+
+using namespace lk;
+
+struct leiden_ctx {
+  cudaStream_t st = nullptr;
+  int device = 0, sms = 152;
+  int64_t max_n = 0, max_nnz = 0;
+  TierTable tiers{};
+  std::vector<void *> allocs;
+  // vertex arrays
+  int32_t *Ctop, *Cp, *CB, *rep;
+  int64_t *Kp, *Sp, *S2, *K0, *Ktmp;
+  uint8_t *ch, *ch2, *processed, *affected, *stamp, *flag;
+  int32_t *prop_i, *prop_c;
+  i128 *prop_S;
+  int32_t *vlist, *clist, *cv;
+  int64_t *ccount, *coff, *ctdeg, *hoff, *cdist, *ccur, *off2tmp;
+  int64_t *scanned, *koff_dev, *scan_tmp;
+  int32_t *blockhist;
+  // level graphs (ping-pong) and aggregation scratch
+  int64_t *goff[2];
+  int32_t *gidx[2];
+  int64_t *gw[2];
+  int32_t *hidx;
+  int64_t *hw;
+  int32_t *gkeys;
+  u64 *gvals;
+  int64_t gcap = 0;
+  u64 *ctr;
+  // pinned host
+  u64 *h_ctr;
+  int64_t *h_koff;
+  // diagnostics of the last failure
+  char err[256] = {0};
+  // statistics
+  leiden_run_stats stats{};
+  int timing = 0;
+  std::vector<cudaEvent_t> evs;
+};
+
+namespace {
+
+constexpr int MAX_KEYS = 256 * MAX_TIERS;
+
+int dalloc(leiden_ctx *c, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return LEIDEN_ENOMEM;
+  }
+  c->allocs.push_back(*p);
+  return LEIDEN_OK;
+}
+
+template <typename T>
+int dal(leiden_ctx *c, T **p, int64_t count) {
+  return dalloc(c, reinterpret_cast<void **>(p), (size_t)count * sizeof(T));
+}
+
+void free_all(leiden_ctx *c) {
+  for (void *p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  if (c->h_ctr) cudaFreeHost(c->h_ctr);
+  if (c->h_koff) cudaFreeHost(c->h_koff);
+  for (auto e : c->evs) cudaEventDestroy(e);
+  c->evs.clear();
+  c->h_ctr = nullptr;
+  c->h_koff = nullptr;
+}
+
+int sync(leiden_ctx *c) {
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return LEIDEN_ECUDA;
+  }
+  return LEIDEN_OK;
+}
+
+int check_cuda(leiden_ctx *c) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return LEIDEN_ECUDA;
+  }
+  return LEIDEN_OK;
+}
+
+// Device-side consistency flags (a full hashtable, a bad label): an internal
+// error, reported as LEIDEN_ECUDA with the flag bits in the detail string.
+int check_dev_flags(leiden_ctx *c, u64 flags) {
+  if (!flags) return LEIDEN_OK;
+  snprintf(c->err, sizeof(c->err), "device consistency check failed (flags 0x%llx)", flags);
+  return LEIDEN_ECUDA;
+}
+
+int gamma_ratio(double gamma, int64_t *p, int64_t *q) {
+  const double scaled = gamma * 1048576.0;
+  if (!(gamma > 0.0) || scaled > 9.0e15) return LEIDEN_EINVAL;
+  int64_t pp = (int64_t)scaled;
+  if ((double)pp != scaled) return LEIDEN_EINVAL;
+  int64_t qq = 1048576, a = pp, b = qq;
+  while (b) { int64_t t = a % b; a = b; b = t; }
+  *p = pp / a;
+  *q = qq / a;
+  return LEIDEN_OK;
+}
+
+int check_opts(const leiden_opts *o, int64_t *p, int64_t *q, int *log2S) {
+  if (!o) return LEIDEN_EINVAL;
+  if (o->max_iters < 1 || o->max_passes < 1 || !(o->tol >= 0.0) || !(o->tol_drop > 0.0)) return LEIDEN_EINVAL;
+  if (o->sched != LEIDEN_DET && o->sched != LEIDEN_ASYNC) return LEIDEN_EINVAL;
+  const int S = o->det_subsets;
+  if (S < 1 || S > 256 || (S & (S - 1))) return LEIDEN_EINVAL;
+  int k = 0;
+  while ((1 << k) < S) k++;
+  *log2S = o->sched == LEIDEN_DET ? k : 0;
+  return gamma_ratio(o->gamma, p, q);
+}
+
+int check_graph(leiden_ctx *c, const leiden_csr *g) {
+  if (!g || g->n < 0 || g->nnz < 0 || g->n >= INT32_MAX) return LEIDEN_EINVAL;
+  if (g->n > 0 && (!g->off || (g->nnz > 0 && (!g->idx || !g->w)))) return LEIDEN_EINVAL;
+  if (g->n > c->max_n || g->nnz > c->max_nnz) return LEIDEN_ENOMEM;
+  return LEIDEN_OK;
+}
+
+// Per-run state shared by the phases.
+struct Run {
+  leiden_ctx *c;
+  const leiden_opts *o;
+  int64_t p, q, two_m, A;
+  int log2S;
+  bool wide;  // 128-bit scores needed
+  bool dynamic;
+  const uint8_t *in_range0;  // DS affected range in pass 0
+  int64_t N;                 // vertices of the input graph
+};
+
+double denom(const Run &r) {
+  // sum(S) / (2 m^2 q), with 2 m^2 = (2m)^2 / 2
+  return (double)r.two_m * (double)r.two_m * 0.5 * (double)r.q;
+}
+
+i128 read_i128(const u64 *h) { return (i128)(((unsigned __int128)h[1] << 64) | (unsigned __int128)h[0]); }
+
+template <typename WT>
+MoveArgs<WT> base_args(const Run &r, GraphView<WT> g) {
+  leiden_ctx *c = r.c;
+  MoveArgs<WT> a{};
+  a.g = g;
+  a.C = c->Cp;
+  a.K = c->Kp;
+  a.Sig = c->Sp;
+  a.processed = c->processed;
+  a.in_range = nullptr;
+  a.CB = c->CB;
+  a.changed = c->ch;
+  a.stamp = c->stamp;
+  a.dynamic = 0;
+  a.prop_i = c->prop_i;
+  a.prop_c = c->prop_c;
+  a.prop_S = c->prop_S;
+  a.prop_count = &c->ctr[CTR_PROPS];
+  a.A = r.A;
+  a.p = r.p;
+  a.gkeys = c->gkeys;
+  a.gvals = c->gvals;
+  a.glog2H = 0;
+  a.ctr = c->ctr;
+  return a;
+}
+
+struct Buckets {
+  int64_t koff[MAX_KEYS + 1];
+  int nkeys;
+  int64_t maxdeg;
+};
+
+__global__ void maxdeg_k(const int64_t *off, int64_t n, u64 *out) {
+  u64 m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const u64 d = (u64)(off[i + 1] - off[i]);
+    if (d > m) m = d;
+  }
+  for (int o = 16; o; o >>= 1) {
+    const u64 y = __shfl_xor_sync(FULL_MASK, m, o);
+    if (y > m) m = y;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+__global__ void count_u8_k(const uint8_t *a, int64_t n, u64 *out) {
+  u64 s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] != 0;
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+int64_t count_flags(leiden_ctx *c, const uint8_t *a, int64_t n) {
+  cudaMemsetAsync(&c->ctr[CTR_SCRATCH0], 0, sizeof(u64), c->st);
+  if (n > 0) count_u8_k<<<c->sms * 4, 256, 0, c->st>>>(a, n, &c->ctr[CTR_SCRATCH0]);
+  cudaMemcpyAsync(&c->h_ctr[CTR_SCRATCH0], &c->ctr[CTR_SCRATCH0], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  if (sync(c)) return -1;
+  return (int64_t)c->h_ctr[CTR_SCRATCH0];
+}
+
+int build_buckets(const Run &r, const int64_t *off, int64_t n, Buckets &b) {
+  leiden_ctx *c = r.c;
+  b.nkeys = (1 << r.log2S) * c->tiers.ntiers;
+  launch_buckets(off, n, r.log2S, c->tiers, c->vlist, c->blockhist, c->scanned, c->koff_dev, c->scan_tmp, c->st);
+  cudaMemsetAsync(&c->ctr[CTR_SCRATCH0], 0, sizeof(u64), c->st);
+  if (n > 0) maxdeg_k<<<c->sms * 4, 256, 0, c->st>>>(off, n, &c->ctr[CTR_SCRATCH0]);
+  cudaMemcpyAsync(c->h_koff, c->koff_dev, (size_t)(b.nkeys + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(&c->h_ctr[CTR_SCRATCH0], &c->ctr[CTR_SCRATCH0], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  int rc = sync(c);
+  if (rc) return rc;
+  memcpy(b.koff, c->h_koff, (size_t)(b.nkeys + 1) * sizeof(int64_t));
+  b.maxdeg = (int64_t)c->h_ctr[CTR_SCRATCH0];
+  return LEIDEN_OK;
+}
+
+// Launch the decide kernels of every tier of colour class s.
+template <typename WT, typename ST, bool REFINE, bool ASYNC>
+void decide_class(const Run &r, MoveArgs<WT> a, const Buckets &b, int s) {
+  leiden_ctx *c = r.c;
+  const int nt = c->tiers.ntiers;
+  for (int t = 1; t < nt; t++) {
+    const int key = s * nt + t;
+    a.list = c->vlist + b.koff[key];
+    a.list_n = b.koff[key + 1] - b.koff[key];
+    if (a.list_n <= 0) continue;
+    const Tier &T = c->tiers.t[t];
+    if (T.kind == TIER_GLOBAL) {
+      // one table of 2^lh slots per block, lh fitted to the largest row
+      int lh = 1;
+      while (((int64_t)1 << lh) < 2 * b.maxdeg) lh++;
+      a.glog2H = lh;
+      a.gblocks = (int)std::min<int64_t>(c->sms, c->gcap >> lh);
+    }
+    launch_decide<WT, ST, REFINE, ASYNC>(T, a, c->sms, c->st);
+  }
+}
+
+// Alg. leidenlm.  Returns l_i (or a negative error code).
+template <typename WT, typename ST>
+int local_move(Run &r, GraphView<WT> g, const Buckets &b, bool first_pass, double tau, int64_t *moves_out) {
+  leiden_ctx *c = r.c;
+  const bool async = r.o->sched == LEIDEN_ASYNC;
+  const int nsub = 1 << r.log2S;
+  MoveArgs<WT> a = base_args(r, g);
+  a.in_range = first_pass ? r.in_range0 : nullptr;
+  a.dynamic = (r.dynamic && first_pass) ? 1 : 0;
+  const double den = denom(r);
+  int li = 0;
+  int64_t moves = 0;
+  cudaMemsetAsync(&c->ctr[CTR_MOVES], 0, sizeof(u64), c->st);
+  cudaMemsetAsync(&c->ctr[CTR_SCANNED_ENTRIES], 0, 3 * sizeof(u64), c->st);
+  while (li < r.o->max_iters) {
+    cudaMemsetAsync(&c->ctr[CTR_SUMS_LO], 0, 2 * sizeof(u64), c->st);
+    for (int s = 0; s < nsub; s++) {
+      if (!async) cudaMemsetAsync(&c->ctr[CTR_PROPS], 0, sizeof(u64), c->st);
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (c->timing) {
+        const size_t k = (size_t)c->stats.move_kernel_launches * 2;
+        while (c->evs.size() < k + 2) {
+          cudaEvent_t e;
+          cudaEventCreate(&e);
+          c->evs.push_back(e);
+        }
+        e0 = c->evs[k];
+        e1 = c->evs[k + 1];
+        cudaEventRecord(e0, c->st);
+      }
+      if (async) decide_class<WT, ST, false, true>(r, a, b, s);
+      else decide_class<WT, ST, false, false>(r, a, b, s);
+      if (c->timing) {
+        cudaEventRecord(e1, c->st);
+        c->stats.move_kernel_launches++;
+      }
+      if (!async)
+        launch_apply_moves(c->prop_i, c->prop_c, c->prop_S, c->ctr, c->Cp, c->Kp, c->Sp, c->ch, c->processed,
+                           g.off, g.idx, a.dynamic, c->sms, c->st);
+    }
+    li++;
+    cudaMemcpyAsync(c->h_ctr, c->ctr, CTR_COUNT * sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+    int rc = sync(c);
+    if (rc) return rc;
+    rc = check_dev_flags(c, c->h_ctr[CTR_ERROR]);
+    if (rc) return rc;
+    const i128 sumS = read_i128(&c->h_ctr[CTR_SUMS_LO]);
+    if (r.two_m == 0 || (double)sumS / den <= tau) break;
+  }
+  moves = (int64_t)c->h_ctr[CTR_MOVES];
+  *moves_out = moves;
+  // algorithmic bytes of the decide kernels: per scanned entry idx + w + the
+  // gathered C'[j]; per scanned vertex the list entry, the pruning flag (read
+  // and write), off[i..i+1], C'[i], K'[i] and Sigma'[d]; per distinct
+  // candidate community its Sigma'[c]
+  const int64_t ent = (int64_t)c->h_ctr[CTR_SCANNED_ENTRIES];
+  const int64_t ver = (int64_t)c->h_ctr[CTR_SCANNED_VERTICES];
+  const int64_t cand = (int64_t)c->h_ctr[CTR_CANDIDATES];
+  c->stats.move_scanned_entries += ent;
+  c->stats.move_scanned_vertices += ver;
+  c->stats.move_bytes += (double)ent * (8.0 + sizeof(WT)) + (double)ver * 42.0 + (double)cand * 8.0;
+  return li;
+}
+
+// Alg. leidenre: one sweep (DET: one sub-sweep per colour class).
+template <typename WT, typename ST>
+int refine(Run &r, GraphView<WT> g, const Buckets &b, int64_t *moves_out) {
+  leiden_ctx *c = r.c;
+  const bool async = r.o->sched == LEIDEN_ASYNC;
+  const int nsub = 1 << r.log2S;
+  MoveArgs<WT> a = base_args(r, g);
+  cudaMemsetAsync(&c->ctr[CTR_MOVES], 0, sizeof(u64), c->st);
+  if (!async) cudaMemsetAsync(c->stamp, 0, (size_t)(g.n > 0 ? g.n : 1), c->st);
+  for (int s = 0; s < nsub; s++) {
+    if (async) {
+      decide_class<WT, ST, true, true>(r, a, b, s);
+    } else {
+      cudaMemsetAsync(&c->ctr[CTR_PROPS], 0, sizeof(u64), c->st);
+      // stamps 1..255 name the sub-sweep a vertex proposed in; a stamp only
+      // matters inside its own sub-sweep, so the array is cleared on wrap
+      const uint8_t sv = (uint8_t)(s % 255 + 1);
+      if (s > 0 && sv == 1) cudaMemsetAsync(c->stamp, 0, (size_t)(g.n > 0 ? g.n : 1), c->st);
+      a.stamp_val = sv;
+      decide_class<WT, ST, true, false>(r, a, b, s);
+      launch_apply_refine(c->prop_i, c->prop_c, c->ctr, c->stamp, sv, c->Cp, c->Kp, c->Sp, c->sms, c->st);
+    }
+  }
+  cudaMemcpyAsync(c->h_ctr, c->ctr, CTR_COUNT * sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  int rc = sync(c);
+  if (rc) return rc;
+  rc = check_dev_flags(c, c->h_ctr[CTR_ERROR]);
+  if (rc) return rc;
+  *moves_out = (int64_t)c->h_ctr[CTR_MOVES];
+  return LEIDEN_OK;
+}
+
+AggWork agg_work(leiden_ctx *c) {
+  AggWork w{};
+  w.ccount = c->ccount; w.coff = c->coff; w.ctdeg = c->ctdeg; w.hoff = c->hoff; w.cdist = c->cdist;
+  w.off2tmp = c->off2tmp; w.ccur = c->ccur; w.cv = c->cv; w.clist = c->clist;
+  w.hidx = c->hidx; w.hw = c->hw; w.gkeys = c->gkeys; w.gvals = c->gvals; w.gcap = c->gcap;
+  w.blockhist = c->blockhist; w.scanned = c->scanned; w.koff_dev = c->koff_dev; w.scan_tmp = c->scan_tmp;
+  w.h_koff = c->h_koff; w.Kout = c->Kp; w.ctr = c->ctr; w.sms = c->sms;
+  return w;
+}
+
+// One pass body for a level graph g; returns 1 to stop, 0 to continue with
+// the aggregated graph written to level buffer `dst`, or a negative error.
+template <typename WT, typename ST>
+int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, int64_t *nnz_out) {
+  leiden_ctx *c = r.c;
+  const int64_t nv = g.n;
+  Buckets b;
+  int rc = build_buckets(r, g.off, nv, b);
+  if (rc) return rc;
+  if (b.koff[b.nkeys] != nv) return LEIDEN_ECUDA;
+  if (b.maxdeg > 0) {
+    int lh = 1;
+    while (((int64_t)1 << lh) < 2 * b.maxdeg) lh++;
+    if (((int64_t)1 << lh) > c->gcap) return LEIDEN_ENOMEM;
+  }
+  int64_t moves = 0, rmoves = 0;
+  const int li = local_move<WT, ST>(r, g, b, lp == 0, tau, &moves);
+  if (li < 0) return li;
+  if (lp == 0) c->stats.changed0 = count_flags(c, c->ch, nv);
+  // Alg. leidensr, then the bounds, the break and the refinement
+  launch_subset_renumber(nv, c->Cp, c->Sp, c->S2, c->ch, c->ch2, c->rep, c->st);
+  std::swap(c->Sp, c->S2);
+  std::swap(c->ch, c->ch2);
+  if (nv > 0) cudaMemcpyAsync(c->CB, c->Cp, (size_t)nv * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st);
+  launch_break(nv, c->Cp, c->Kp, c->Sp, c->ch, c->st);
+  rc = refine<WT, ST>(r, g, b, &rmoves);
+  if (rc) return rc;
+  if (lp < LEIDEN_STATS_PASSES) {
+    c->stats.passes = lp + 1;
+    c->stats.iters[lp] = li;
+    c->stats.nv[lp] = nv;
+    c->stats.moves[lp] = moves;
+    c->stats.refine_moves[lp] = rmoves;
+  }
+  if (lp > 0 && li <= 1) return 1;  // globally converged
+  launch_renumber(nv, c->Cp, c->flag, c->scanned, c->scan_tmp, c->ctr, c->st);
+  cudaMemcpyAsync(&c->h_ctr[CTR_NCOMM], &c->ctr[CTR_NCOMM], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  rc = sync(c);
+  if (rc) return rc;
+  const int64_t nc = (int64_t)c->h_ctr[CTR_NCOMM];
+  *nc_out = nc;
+  if (nc == nv) return 1;  // aggregation would not shrink the graph
+  launch_lookup(r.N, c->Ctop, c->Cp, c->st);
+  int64_t nnz2 = 0;
+  rc = aggregate<WT>(g, c->Cp, nc, c->goff[dst], c->gidx[dst], c->gw[dst], &nnz2, agg_work(c), c->st);
+  if (rc) return rc;
+  cudaMemcpyAsync(&c->h_ctr[CTR_ERROR], &c->ctr[CTR_ERROR], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  rc = sync(c);
+  if (rc) return rc;
+  rc = check_dev_flags(c, c->h_ctr[CTR_ERROR]);
+  if (rc) return rc;
+  *nnz_out = nnz2;
+  return 0;
+}
+
+template <typename ST>
+int run_leiden_st(Run &r, const leiden_csr *g0) {
+  leiden_ctx *c = r.c;
+  const int64_t N = g0->n;
+  launch_iota(c->Ctop, N, c->st);
+  double tau = r.o->tol;
+  GraphView<int32_t> g32{N, g0->off, g0->idx, g0->w};
+  GraphView<int64_t> g64{};
+  int cur = -1;  // -1: level 0 (input graph); else level buffer index
+  int64_t nv = N;
+  int lp;
+  int64_t nnz_cur = g0->nnz;
+  for (lp = 0; lp < r.o->max_passes; lp++) {
+    if (lp < LEIDEN_STATS_PASSES) c->stats.nnz[lp] = nnz_cur;
+    const int dst = cur < 0 ? 0 : 1 - cur;
+    int64_t nc = 0, nnz2 = 0;
+    int rc = cur < 0 ? pass<int32_t, ST>(r, g32, lp, tau, dst, &nc, &nnz2)
+                     : pass<int64_t, ST>(r, g64, lp, tau, dst, &nc, &nnz2);
+    if (rc < 0) return rc;
+    if (rc == 1) break;
+    // next level: K' = Sigma' = row sums (written by the aggregation), C' =
+    // identity, everything unprocessed, every community changed
+    cur = dst;
+    g64 = GraphView<int64_t>{nc, c->goff[cur], c->gidx[cur], c->gw[cur]};
+    nv = nc;
+    nnz_cur = nnz2;
+    launch_copy_i64(c->Sp, c->Kp, nv, c->st);
+    launch_iota(c->Cp, nv, c->st);
+    cudaMemsetAsync(c->processed, 0, (size_t)(nv > 0 ? nv : 1), c->st);
+    cudaMemsetAsync(c->ch, 1, (size_t)(nv > 0 ? nv : 1), c->st);
+    tau /= r.o->tol_drop;
+  }
+  launch_lookup(N, c->Ctop, c->Cp, c->st);
+  return check_cuda(c);
+}
+
+int run_leiden(Run &r, const leiden_csr *g0) {
+  // the level-0 nnz is recorded by the caller's stats; the first pass uses the
+  // input graph directly (int32 weights), later passes the workspace (int64)
+  if (r.wide) return run_leiden_st<i128>(r, g0);
+  return run_leiden_st<int64_t>(r, g0);
+}
+
+// Device-side validation of a caller's CSR (off, idx, w); LEIDEN_EINVAL on a
+// malformed graph.  One read of the graph, so the kernels after it can index
+// by the graph's own IDs without further checks.
+int validate_graph(leiden_ctx *c, const leiden_csr *g) {
+  cudaMemsetAsync(&c->ctr[CTR_ERROR], 0, sizeof(u64), c->st);
+  launch_check_graph(g->n, g->nnz, g->off, g->idx, g->w, &c->ctr[CTR_ERROR], c->st);
+  cudaMemcpyAsync(&c->h_ctr[CTR_ERROR], &c->ctr[CTR_ERROR], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  int rc = sync(c);
+  if (rc) return rc;
+  if (c->h_ctr[CTR_ERROR]) {
+    snprintf(c->err, sizeof(c->err), "malformed CSR (flags 0x%llx)", c->h_ctr[CTR_ERROR]);
+    cudaMemsetAsync(&c->ctr[CTR_ERROR], 0, sizeof(u64), c->st);
+    return LEIDEN_EINVAL;
+  }
+  return LEIDEN_OK;
+}
+
+int setup_run(leiden_ctx *c, const leiden_csr *g, const leiden_opts *o, Run &r) {
+  r.c = c;
+  r.o = o;
+  c->err[0] = 0;
+  int rc = check_opts(o, &r.p, &r.q, &r.log2S);
+  if (rc) return rc;
+  rc = check_graph(c, g);
+  if (rc) return rc;
+  rc = validate_graph(c, g);
+  if (rc) return rc;
+  r.N = g->n;
+  return LEIDEN_OK;
+}
+
+int finish_two_m(leiden_ctx *c, Run &r, const leiden_csr *g) {
+  // 2m = total CSR weight of G^t, from its row sums (K0)
+  cudaMemsetAsync(&c->ctr[CTR_SCRATCH0], 0, sizeof(u64), c->st);
+  launch_sum_i64(c->K0, g->n, &c->ctr[CTR_SCRATCH0], c->st);
+  cudaMemcpyAsync(&c->h_ctr[CTR_SCRATCH0], &c->ctr[CTR_SCRATCH0], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  int rc = sync(c);
+  if (rc) return rc;
+  r.two_m = (int64_t)c->h_ctr[CTR_SCRATCH0];
+  if (r.two_m < 0 || r.two_m >= ((int64_t)1 << 40)) return LEIDEN_EOVERFLOW;
+  r.A = r.two_m * r.q;
+  const i128 bound = (i128)4 * r.two_m * r.two_m * (r.p > r.q ? r.p : r.q);
+  r.wide = bound >= ((i128)1 << 62);
+  return LEIDEN_OK;
+}
+
+int modularity_of(leiden_ctx *c, const leiden_csr *g, const int32_t *C, int64_t p, int64_t q, double *q_out) {
+  GraphView<int32_t> gv{g->n, g->off, g->idx, g->w};
+  launch_modularity_terms(gv, C, c->Ktmp, &c->ctr[CTR_SCRATCH0], c->st);
+  cudaMemcpyAsync(&c->h_ctr[CTR_SCRATCH0], &c->ctr[CTR_SCRATCH0], 4 * sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  int rc = sync(c);
+  if (rc) return rc;
+  const int64_t inside = (int64_t)c->h_ctr[CTR_SCRATCH0];
+  const i128 sq = read_i128(&c->h_ctr[CTR_SCRATCH0 + 1]);
+  const int64_t two_m = (int64_t)c->h_ctr[CTR_SCRATCH0 + 3];
+  const i128 num = (i128)q * two_m * inside - (i128)p * sq;
+  *q_out = two_m == 0 ? 0.0 : (double)num / ((double)two_m * (double)two_m * (double)q);
+  return LEIDEN_OK;
+}
+
+void reset_stats(leiden_ctx *c) {
+  c->stats = leiden_run_stats{};
+}
+
+void finish_timing(leiden_ctx *c) {
+  if (!c->timing) return;
+  double ms = 0;
+  for (int64_t k = 0; k < c->stats.move_kernel_launches; k++) {
+    float t = 0;
+    cudaEventElapsedTime(&t, c->evs[2 * k], c->evs[2 * k + 1]);
+    ms += t;
+  }
+  c->stats.move_kernel_ms = ms;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+void leiden_opts_default(leiden_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->gamma = 1.0;
+  o->tol = 0.01;
+  o->tol_drop = 10.0;
+  o->max_iters = 20;
+  o->max_passes = 10;
+  o->sched = LEIDEN_DET;
+  o->det_subsets = 8;
+  o->refine_all_first_pass = 0;
+}
+
+const char *leiden_strerror(int code) {
+  switch (code) {
+    case LEIDEN_OK: return "ok";
+    case LEIDEN_EINVAL: return "invalid argument";
+    case LEIDEN_ENOMEM: return "exceeds capacity or out of memory";
+    case LEIDEN_EOVERFLOW: return "total edge weight too large (2m >= 2^40)";
+    case LEIDEN_ETIMEOUT: return "bounded device wait expired";
+    case LEIDEN_ECUDA: return "CUDA error";
+    default: return "unknown error";
+  }
+}
+
+int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_t max_nnz) {
+  if (!out || max_n < 0 || max_nnz < 0 || max_n >= INT32_MAX) return LEIDEN_EINVAL;
+  *out = nullptr;
+  leiden_ctx *c = new leiden_ctx();
+  c->st = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return LEIDEN_ECUDA; }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  c->max_n = max_n;
+  c->max_nnz = max_nnz;
+  c->tiers = default_tiers();
+  const int64_t n1 = max_n + 1, m = max_nnz > 0 ? max_nnz : 1;
+  const int64_t bh = bucket_blockhist_elems(max_n, MAX_KEYS);
+  const int64_t scan_n = std::max<int64_t>(bh, 4 * n1 + 4);
+  c->gcap = std::max<int64_t>(m, (int64_t)1 << 22);
+  int rc = LEIDEN_OK;
+  rc |= dal(c, &c->Ctop, n1); rc |= dal(c, &c->Cp, n1); rc |= dal(c, &c->CB, n1); rc |= dal(c, &c->rep, n1);
+  rc |= dal(c, &c->Kp, n1); rc |= dal(c, &c->Sp, n1); rc |= dal(c, &c->S2, n1); rc |= dal(c, &c->K0, n1);
+  rc |= dal(c, &c->Ktmp, n1);
+  rc |= dal(c, &c->ch, n1 + 16); rc |= dal(c, &c->ch2, n1 + 16); rc |= dal(c, &c->processed, n1 + 16);
+  rc |= dal(c, &c->affected, n1 + 16); rc |= dal(c, &c->stamp, n1 + 16); rc |= dal(c, &c->flag, n1 + 16);
+  rc |= dal(c, &c->prop_i, n1); rc |= dal(c, &c->prop_c, n1); rc |= dal(c, &c->prop_S, n1);
+  rc |= dal(c, &c->vlist, n1); rc |= dal(c, &c->clist, n1); rc |= dal(c, &c->cv, n1);
+  rc |= dal(c, &c->ccount, n1); rc |= dal(c, &c->coff, n1); rc |= dal(c, &c->ctdeg, n1);
+  rc |= dal(c, &c->hoff, n1); rc |= dal(c, &c->cdist, n1); rc |= dal(c, &c->ccur, n1);
+  rc |= dal(c, &c->off2tmp, 4 * n1 + 4);
+  rc |= dal(c, &c->scanned, scan_n + 1); rc |= dal(c, &c->koff_dev, MAX_KEYS + 1);
+  rc |= dal(c, &c->scan_tmp, scan_tmp_elems(scan_n) + 1);
+  rc |= dal(c, &c->blockhist, bh);
+  for (int k = 0; k < 2; k++) {
+    rc |= dal(c, &c->goff[k], n1); rc |= dal(c, &c->gidx[k], m); rc |= dal(c, &c->gw[k], m);
+  }
+  rc |= dal(c, &c->hidx, m); rc |= dal(c, &c->hw, m);
+  rc |= dal(c, &c->gkeys, c->gcap); rc |= dal(c, &c->gvals, c->gcap);
+  rc |= dal(c, &c->ctr, CTR_COUNT);
+  if (rc == LEIDEN_OK) {
+    if (cudaMallocHost((void **)&c->h_ctr, CTR_COUNT * sizeof(u64)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_koff, (MAX_KEYS + 8) * sizeof(int64_t)) != cudaSuccess)
+      rc = LEIDEN_ENOMEM;
+  }
+  if (rc != LEIDEN_OK) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return LEIDEN_ENOMEM;
+  }
+  cudaMemsetAsync(c->ctr, 0, CTR_COUNT * sizeof(u64), c->st);
+  if (sync(c)) { free_all(c); delete c; return LEIDEN_ECUDA; }
+  *out = c;
+  return LEIDEN_OK;
+}
+
+void leiden_ctx_destroy(leiden_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  free_all(c);
+  delete c;
+}
+
+int leiden_ctx_set_timing(leiden_ctx *c, int32_t enable) {
+  if (!c) return LEIDEN_EINVAL;
+  c->timing = enable ? 1 : 0;
+  return LEIDEN_OK;
+}
+
+const char *leiden_ctx_last_error(leiden_ctx *c) {
+  if (!c) return "no context";
+  return c->err;
+}
+
+int leiden_get_stats(leiden_ctx *c, leiden_run_stats *out) {
+  if (!c || !out) return LEIDEN_EINVAL;
+  *out = c->stats;
+  return LEIDEN_OK;
+}
+
+int leiden_static(leiden_ctx *c, const leiden_csr *g, const leiden_opts *o, int32_t *membership_out,
+                  double *q_out) {
+  if (!c || (!membership_out && g && g->n > 0)) return LEIDEN_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  Run r{};
+  int rc = setup_run(c, g, o, r);
+  if (rc) return rc;
+  reset_stats(c);
+  const int64_t n = g->n;
+  GraphView<int32_t> gv{n, g->off, g->idx, g->w};
+  launch_row_sums(gv, c->K0, c->st);
+  rc = finish_two_m(c, r, g);
+  if (rc) return rc;
+  // Static: C' = identity, K' = K, Sigma' = K, every community changed,
+  // every vertex affected and in range
+  launch_copy_i64(c->Kp, c->K0, n, c->st);
+  launch_copy_i64(c->Sp, c->K0, n, c->st);
+  launch_iota(c->Cp, n, c->st);
+  cudaMemsetAsync(c->ch, 1, (size_t)(n > 0 ? n : 1), c->st);
+  cudaMemsetAsync(c->processed, 0, (size_t)(n > 0 ? n : 1), c->st);
+  r.dynamic = false;
+  r.in_range0 = nullptr;
+  c->stats.affected0 = n;
+  rc = run_leiden(r, g);
+  if (rc) return rc;
+  launch_canonical(n, c->Ctop, membership_out, c->rep, c->flag, c->scanned, c->scan_tmp, c->st);
+  rc = sync(c);
+  if (rc) return rc;
+  if (q_out) {
+    rc = modularity_of(c, g, membership_out, r.p, r.q, q_out);
+    if (rc) return rc;
+  }
+  finish_timing(c);
+  c->stats.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return LEIDEN_OK;
+}
+
+int leiden_update(leiden_ctx *c, const leiden_csr *g, const int32_t *prior_membership, const int64_t *prior_K,
+                  const int64_t *prior_Sigma, const leiden_edges *del, const leiden_edges *ins, int32_t mode,
+                  const leiden_opts *o, int32_t *membership_out, int64_t *K_out, int64_t *Sigma_out,
+                  double *q_out) {
+  if (!c) return LEIDEN_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  Run r{};
+  int rc = setup_run(c, g, o, r);
+  if (rc) return rc;
+  if (mode != LEIDEN_ND && mode != LEIDEN_DS && mode != LEIDEN_DF) return LEIDEN_EINVAL;
+  const int64_t n = g->n;
+  if (n > 0 && (!prior_membership || !membership_out)) return LEIDEN_EINVAL;
+  if ((prior_K == nullptr) != (prior_Sigma == nullptr)) return LEIDEN_EINVAL;
+  const int64_t nd = del ? del->count : 0, ni = ins ? ins->count : 0;
+  if (nd < 0 || ni < 0) return LEIDEN_EINVAL;
+  if ((nd > 0 && (!del->src || !del->dst || !del->w)) || (ni > 0 && (!ins->src || !ins->dst || !ins->w)))
+    return LEIDEN_EINVAL;
+  if (2 * ni > c->max_nnz || 2 * nd > c->max_nnz) return LEIDEN_ENOMEM;
+  reset_stats(c);
+  // batch IDs must lie in [0, n), no self-loops, positive weights
+  cudaMemsetAsync(&c->ctr[CTR_ERROR], 0, sizeof(u64), c->st);
+  if (nd) launch_check_ids(nd, del->src, del->dst, del->w, n, &c->ctr[CTR_ERROR], c->st);
+  if (ni) launch_check_ids(ni, ins->src, ins->dst, ins->w, n, &c->ctr[CTR_ERROR], c->st);
+  launch_check_range(prior_membership, n, n, &c->ctr[CTR_ERROR], c->st);
+  cudaMemcpyAsync(&c->h_ctr[CTR_ERROR], &c->ctr[CTR_ERROR], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  rc = sync(c);
+  if (rc) return rc;
+  if (c->h_ctr[CTR_ERROR]) {
+    snprintf(c->err, sizeof(c->err), "batch IDs or prior labels out of range (flags 0x%llx)",
+             c->h_ctr[CTR_ERROR]);
+    cudaMemsetAsync(&c->ctr[CTR_ERROR], 0, sizeof(u64), c->st);
+    return LEIDEN_EINVAL;
+  }
+
+  GraphView<int32_t> gv{n, g->off, g->idx, g->w};
+  launch_row_sums(gv, c->K0, c->st);  // K^t of G^t, also the source of 2m
+  rc = finish_two_m(c, r, g);
+  if (rc) return rc;
+  // Alg. update: K^t, Sigma^t from the auxiliary information, or recomputed
+  if (prior_K) {
+    launch_copy_i64(c->Kp, prior_K, n, c->st);
+    launch_copy_i64(c->Sp, prior_Sigma, n, c->st);
+    if (nd) launch_update_weights(nd, del->src, del->dst, del->w, -1, prior_membership, c->Kp, c->Sp, c->st);
+    if (ni) launch_update_weights(ni, ins->src, ins->dst, ins->w, +1, prior_membership, c->Kp, c->Sp, c->st);
+    launch_copy_i64(c->K0, c->Kp, n, c->st);  // K^t as Alg. update gives it
+  } else {
+    launch_copy_i64(c->Kp, c->K0, n, c->st);
+    launch_sigma_from(n, prior_membership, c->Kp, c->Sp, c->st);
+  }
+  // changedCommunities (Alg. leiden, dynamic branch)
+  cudaMemsetAsync(c->ch, 0, (size_t)(n > 0 ? n : 1), c->st);
+  if (!o->refine_all_first_pass) {
+    if (nd) launch_changed_communities(nd, del->src, del->dst, prior_membership, c->ch, c->st);
+    if (ni) launch_changed_communities(ni, ins->src, ins->dst, prior_membership, c->ch, c->st);
+  } else {
+    cudaMemsetAsync(c->ch, 1, (size_t)(n > 0 ? n : 1), c->st);
+  }
+  // affected vertices (Alg. naive / delta / frontier)
+  r.in_range0 = nullptr;
+  if (mode == LEIDEN_ND) {
+    cudaMemsetAsync(c->processed, 0, (size_t)(n > 0 ? n : 1), c->st);
+  } else {
+    cudaMemsetAsync(c->affected, 0, (size_t)(n > 0 ? n : 1), c->st);
+    if (mode == LEIDEN_DF) {
+      if (nd) launch_mark_df(nd, del->src, del->dst, prior_membership, 1, c->affected, c->st);
+      if (ni) launch_mark_df(ni, ins->src, ins->dst, prior_membership, 0, c->affected, c->st);
+    } else {
+      DsWork w{};
+      w.cnt = c->ccount; w.soff = c->coff; w.cur = c->ccur;
+      w.sdst = c->hidx; w.swt = reinterpret_cast<int32_t *>(c->hw);
+      w.scan_tmp = c->scan_tmp; w.dE = c->flag; w.dC = c->stamp;
+      launch_mark_ds(n, g->off, g->idx, prior_membership, c->Kp, c->Sp, r.A, r.p, nd, nd ? del->src : nullptr,
+                     nd ? del->dst : nullptr, ni, ni ? ins->src : nullptr, ni ? ins->dst : nullptr,
+                     ni ? ins->w : nullptr, c->affected, w, c->st);
+      r.in_range0 = c->affected;
+    }
+    launch_invert_u8(c->processed, c->affected, n, c->st);
+  }
+  if (n > 0) cudaMemcpyAsync(c->Cp, prior_membership, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st);
+  c->stats.affected0 = mode == LEIDEN_ND ? n : count_flags(c, c->affected, n);
+  r.dynamic = true;
+  rc = run_leiden(r, g);
+  if (rc) return rc;
+  launch_canonical(n, c->Ctop, membership_out, c->rep, c->flag, c->scanned, c->scan_tmp, c->st);
+  if (K_out) launch_copy_i64(K_out, c->K0, n, c->st);
+  if (Sigma_out) launch_sigma_from(n, membership_out, c->K0, Sigma_out, c->st);
+  rc = sync(c);
+  if (rc) return rc;
+  if (q_out) {
+    rc = modularity_of(c, g, membership_out, r.p, r.q, q_out);
+    if (rc) return rc;
+  }
+  finish_timing(c);
+  c->stats.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return LEIDEN_OK;
+}
+
+int leiden_modularity(leiden_ctx *c, const leiden_csr *g, const int32_t *membership, double gamma, double *q_out) {
+  if (!c || !q_out) return LEIDEN_EINVAL;
+  int rc = check_graph(c, g);
+  if (rc) return rc;
+  if (g->n > 0 && !membership) return LEIDEN_EINVAL;
+  rc = validate_graph(c, g);
+  if (rc) return rc;
+  cudaMemsetAsync(&c->ctr[CTR_ERROR], 0, sizeof(u64), c->st);
+  launch_check_range(membership, g->n, g->n, &c->ctr[CTR_ERROR], c->st);
+  cudaMemcpyAsync(&c->h_ctr[CTR_ERROR], &c->ctr[CTR_ERROR], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  rc = sync(c);
+  if (rc) return rc;
+  if (c->h_ctr[CTR_ERROR]) {
+    cudaMemsetAsync(&c->ctr[CTR_ERROR], 0, sizeof(u64), c->st);
+    return LEIDEN_EINVAL;
+  }
+  int64_t p, q;
+  rc = gamma_ratio(gamma, &p, &q);
+  if (rc) return rc;
+  return modularity_of(c, g, membership, p, q, q_out);
+}
+
+int leiden_apply_batch(leiden_ctx *c, const leiden_csr *g, const leiden_edges *del, const leiden_edges *ins,
+                       int64_t *off_out, int32_t *idx_out, int32_t *w_out, int64_t cap_nnz, int64_t *nnz_out) {
+  if (!c || !off_out || !nnz_out || cap_nnz < 0) return LEIDEN_EINVAL;
+  int rc = check_graph(c, g);
+  if (rc) return rc;
+  const int64_t nd = del ? del->count : 0, ni = ins ? ins->count : 0;
+  if (nd < 0 || ni < 0) return LEIDEN_EINVAL;
+  if ((nd > 0 && (!del->src || !del->dst || !del->w)) || (ni > 0 && (!ins->src || !ins->dst || !ins->w)))
+    return LEIDEN_EINVAL;
+  if (2 * ni > c->max_nnz) return LEIDEN_ENOMEM;
+  if (cap_nnz > 0 && (!idx_out || !w_out)) return LEIDEN_EINVAL;
+  rc = validate_graph(c, g);
+  if (rc) return rc;
+  BatchWork w{};
+  w.cnt = c->ccount; w.ioff = c->coff; w.cur = c->ccur;
+  w.idst = c->hidx; w.iwt = reinterpret_cast<int32_t *>(c->hw);
+  w.newdeg = c->ctdeg;
+  w.delmark = reinterpret_cast<uint8_t *>(c->gvals);
+  w.scan_tmp = c->scan_tmp;
+  w.err = &c->ctr[CTR_ERROR];
+  return apply_batch(g->n, g->off, g->idx, g->w, nd, nd ? del->src : nullptr, nd ? del->dst : nullptr,
+                     nd ? del->w : nullptr, ni, ni ? ins->src : nullptr, ni ? ins->dst : nullptr,
+                     ni ? ins->w : nullptr, off_out, idx_out, w_out, cap_nnz, nnz_out, w, c->st);
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// common.cuh -- device-side helpers shared by the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+typedef __int128 i128;
+typedef unsigned long long u64;
+
+#define LEIDEN_EMPTY_KEY (-1)
+#define FULL_MASK 0xffffffffu
+
+namespace lk {
+
+// Multiplicative hash of a community ID; the top bits index the table.
+__device__ __forceinline__ uint32_t hash32(int32_t c) {
+  return (uint32_t)c * 0x9E3779B1u;
+}
+
+// DET colour class: top log2(S) bits of (uint32)(i * 2654435761).
+__host__ __device__ __forceinline__ int det_class(int32_t i, int log2S) {
+  if (log2S == 0) return 0;
+  uint32_t h = (uint32_t)i * 2654435761u;
+  return (int)(h >> (32 - log2S));
+}
+
+__device__ __forceinline__ int64_t shfl_xor_i64(int64_t v, int off) {
+  return (int64_t)__shfl_xor_sync(FULL_MASK, (long long)v, off);
+}
+__device__ __forceinline__ int64_t shfl_i64(int64_t v, int src) {
+  return (int64_t)__shfl_sync(FULL_MASK, (long long)v, src);
+}
+__device__ __forceinline__ i128 shfl_xor_i128(i128 v, int off) {
+  long long lo = (long long)(u64)v;
+  long long hi = (long long)(v >> 64);
+  lo = __shfl_xor_sync(FULL_MASK, lo, off);
+  hi = __shfl_xor_sync(FULL_MASK, hi, off);
+  return ((i128)hi << 64) | (i128)(u64)lo;
+}
+__device__ __forceinline__ i128 shfl_i128(i128 v, int src) {
+  long long lo = (long long)(u64)v;
+  long long hi = (long long)(v >> 64);
+  lo = __shfl_sync(FULL_MASK, lo, src);
+  hi = __shfl_sync(FULL_MASK, hi, src);
+  return ((i128)hi << 64) | (i128)(u64)lo;
+}
+template <typename T> __device__ __forceinline__ T shfl_xor_any(T v, int off);
+template <> __device__ __forceinline__ int64_t shfl_xor_any<int64_t>(int64_t v, int off) { return shfl_xor_i64(v, off); }
+template <> __device__ __forceinline__ i128 shfl_xor_any<i128>(i128 v, int off) { return shfl_xor_i128(v, off); }
+template <typename T> __device__ __forceinline__ T shfl_any(T v, int src);
+template <> __device__ __forceinline__ int64_t shfl_any<int64_t>(int64_t v, int src) { return shfl_i64(v, src); }
+template <> __device__ __forceinline__ i128 shfl_any<i128>(i128 v, int src) { return shfl_i128(v, src); }
+
+// Exact signed 128-bit accumulation into two 64-bit words with two atomics:
+// the word that wraps is detected by the adder that wrapped it, so every carry
+// is counted exactly once and the pair holds the sum modulo 2^128.
+__device__ __forceinline__ void atomic_add_i128(u64 *acc /* [lo, hi] */, i128 x) {
+  u64 lo = (u64)x;
+  u64 hi = (u64)(x >> 64);
+  u64 old = atomicAdd(&acc[0], lo);
+  u64 carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(&acc[1], hi + carry);
+}
+
+__device__ __forceinline__ void atomic_add_i64(int64_t *p, int64_t v) {
+  atomicAdd((u64 *)p, (u64)v);
+}
+
+// Warp-aggregated reservation of `want` (0/1 per lane) slots in a counter;
+// returns this lane's slot (valid where want != 0).  Whole warp must call.
+__device__ __forceinline__ u64 warp_reserve(u64 *counter, bool want) {
+  unsigned m = __ballot_sync(FULL_MASK, want);
+  if (!m) return 0;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(m) - 1;
+  u64 base = 0;
+  if (lane == leader) base = atomicAdd(counter, (u64)__popc(m));
+  base = __shfl_sync(FULL_MASK, base, leader);
+  return base + __popc(m & ((1u << lane) - 1u));
+}
+
+// Block-wide sum of an i128 (every thread of the block must call); the result
+// is valid in thread 0.  Uses 32 * 16 bytes of the given shared buffer.
+__device__ __forceinline__ i128 block_sum_i128(i128 v, i128 *sbuf) {
+  for (int o = 16; o; o >>= 1) v += shfl_xor_i128(v, o);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sbuf[warp] = v;
+  __syncthreads();
+  i128 r = 0;
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < nw; k++) r += sbuf[k];
+  }
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int64_t block_sum_i64(int64_t v, int64_t *sbuf) {
+  for (int o = 16; o; o >>= 1) v += shfl_xor_i64(v, o);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sbuf[warp] = v;
+  __syncthreads();
+  int64_t r = 0;
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < nw; k++) r += sbuf[k];
+  }
+  __syncthreads();
+  return r;
+}
+
+}  // namespace lk

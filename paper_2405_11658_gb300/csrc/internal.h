@@ -1,0 +1,209 @@
+// internal.h -- host-side interface between the C-ABI driver (api.cu) and the
+// kernel launchers of the other translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "leiden.h"
+
+typedef __int128 i128;
+typedef unsigned long long u64;
+
+namespace lk {
+
+// ---------------------------------------------------------------------------
+// Degree tiers of the local-move / refinement kernels.  A vertex of degree d
+// (CSR entries, self-loop included) goes to the first tier with d <= maxdeg.
+// Tier 0 holds isolated vertices and is never launched.  "group" tiers give a
+// vertex G lanes of a warp and an H-slot shared-memory table; "block" tiers
+// give it a whole block; the last tier keeps its table in global scratch.
+// ---------------------------------------------------------------------------
+enum TierKind { TIER_SKIP = 0, TIER_GROUP = 1, TIER_BLOCK = 2, TIER_GLOBAL = 3 };
+struct Tier {
+  int kind;
+  int64_t maxdeg;
+  int G;        // lanes per vertex (group tiers)
+  int log2H;    // table slots (group / block tiers)
+  int threads;  // block size
+};
+static constexpr int MAX_TIERS = 12;
+struct TierTable {
+  int ntiers;
+  Tier t[MAX_TIERS];
+};
+TierTable default_tiers();
+
+template <typename WT>
+struct GraphView {
+  int64_t n;
+  const int64_t *off;
+  const int32_t *idx;
+  const WT *w;
+};
+
+// Arguments of the local-move and refinement kernels (Alg. leidenlm,
+// Alg. leidenre).  Scores are Eq. 2 scaled by 2m^2 q:
+//   S = A (K_{i->c} - K_{i->d}) - p K_i (K_i + Sigma_c - Sigma_d),  A = 2m q.
+template <typename WT>
+struct MoveArgs {
+  GraphView<WT> g;
+  const int32_t *list;   // vertices of one (class, tier) bucket
+  int64_t list_n;
+  int32_t *C;            // C'
+  const int64_t *K;      // K'
+  int64_t *Sig;          // Sigma'
+  uint8_t *processed;    // vertex pruning flags (local-move)
+  const uint8_t *in_range;  // DS affected range in pass 0, else NULL
+  const int32_t *CB;     // community bounds (refinement)
+  uint8_t *changed;      // Delta C'
+  uint8_t *stamp;        // refinement: sub-sweep in which a vertex proposed
+  uint8_t stamp_val;
+  int dynamic;           // mark changed communities on migration
+  int32_t *prop_i;       // DET proposals
+  int32_t *prop_c;
+  i128 *prop_S;
+  u64 *prop_count;
+  int64_t A;             // 2m * q
+  int64_t p;
+  int32_t *gkeys;        // global-table tier scratch: gblocks tables of 2^glog2H slots
+  u64 *gvals;
+  int glog2H;
+  int gblocks;
+  u64 *ctr;              // counters, see CTR_*
+};
+
+enum {
+  CTR_SCANNED_ENTRIES = 0,
+  CTR_SCANNED_VERTICES = 1,
+  CTR_CANDIDATES = 2,
+  CTR_SUMS_LO = 3,      // i128 sum of S over applied moves (lo, hi)
+  CTR_SUMS_HI = 4,
+  CTR_MOVES = 5,
+  CTR_PROPS = 6,        // proposal count of the current sub-sweep
+  CTR_ERROR = 7,
+  CTR_NCOMM = 8,
+  CTR_SCRATCH0 = 9,
+  CTR_COUNT = 16
+};
+
+// move.cu
+template <typename WT, typename ST, bool REFINE, bool ASYNC>
+void launch_decide(const Tier &tier, const MoveArgs<WT> &a, int sms, cudaStream_t s);
+void launch_apply_moves(const int32_t *prop_i, const int32_t *prop_c, const i128 *prop_S,
+                        u64 *ctr, int32_t *C, const int64_t *K, int64_t *Sig,
+                        uint8_t *changed, uint8_t *processed, const int64_t *off,
+                        const int32_t *idx, int dynamic, int sms, cudaStream_t s);
+void launch_apply_refine(const int32_t *prop_i, const int32_t *prop_c, u64 *ctr,
+                         const uint8_t *stamp, uint8_t sv, int32_t *C, const int64_t *K,
+                         int64_t *Sig, int sms, cudaStream_t s);
+
+// buckets.cu
+// Builds the vertex lists of every (class, tier) key, key = class * ntiers + tier,
+// stored key-major in `list`; koff_dev[key] / koff_dev[nkeys] are the offsets.
+void launch_buckets(const int64_t *off, int64_t n, int log2S, const TierTable &tt,
+                    int32_t *list, int32_t *blockhist, int64_t *scanned, int64_t *koff_dev,
+                    int64_t *scan_tmp, cudaStream_t s);
+int64_t bucket_blockhist_elems(int64_t n, int nkeys);
+
+// scan.cu
+template <typename TI>
+void exclusive_scan(const TI *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+int64_t scan_tmp_elems(int64_t n);
+
+// misc.cu
+template <typename WT>
+void launch_row_sums(GraphView<WT> g, int64_t *K, cudaStream_t s);
+void launch_iota(int32_t *a, int64_t n, cudaStream_t s);
+void launch_fill_u8(uint8_t *a, uint8_t v, int64_t n, cudaStream_t s);
+void launch_copy_i64(int64_t *dst, const int64_t *src, int64_t n, cudaStream_t s);
+void launch_invert_u8(uint8_t *dst, const uint8_t *src, int64_t n, cudaStream_t s);
+void launch_sum_i64(const int64_t *a, int64_t n, u64 *out, cudaStream_t s);
+void launch_subset_renumber(int64_t n, int32_t *C, const int64_t *Sig, int64_t *Sig2,
+                            const uint8_t *ch, uint8_t *ch2, int32_t *rep, cudaStream_t s);
+void launch_break(int64_t n, int32_t *C, const int64_t *K, int64_t *Sig, const uint8_t *ch,
+                  cudaStream_t s);
+// dense renumbering; returns |Gamma| in ctr[CTR_NCOMM] (device)
+void launch_renumber(int64_t n, int32_t *C, uint8_t *exists, int64_t *scanned, int64_t *tmp,
+                     u64 *ctr, cudaStream_t s);
+void launch_lookup(int64_t n, int32_t *Ctop, const int32_t *Cp, cudaStream_t s);
+void launch_canonical(int64_t n, const int32_t *C, int32_t *out, int32_t *minv, uint8_t *flag,
+                      int64_t *scanned, int64_t *tmp, cudaStream_t s);
+template <typename WT>
+void launch_modularity_terms(GraphView<WT> g, const int32_t *C, int64_t *Sig_tmp, u64 *acc,
+                             cudaStream_t s);
+void launch_update_weights(int64_t count, const int32_t *src, const int32_t *dst,
+                           const int32_t *w, int sign, const int32_t *Cprev, int64_t *K,
+                           int64_t *Sig, cudaStream_t s);
+void launch_changed_communities(int64_t count, const int32_t *src, const int32_t *dst,
+                                const int32_t *Cprev, uint8_t *changed, cudaStream_t s);
+void launch_mark_df(int64_t count, const int32_t *src, const int32_t *dst, const int32_t *Cprev,
+                    int same, uint8_t *affected, cudaStream_t s);
+void launch_check_ids(int64_t count, const int32_t *src, const int32_t *dst, const int32_t *w,
+                      int64_t n, u64 *err, cudaStream_t s);
+void launch_check_graph(int64_t n, int64_t nnz, const int64_t *off, const int32_t *idx, const int32_t *w,
+                        u64 *err, cudaStream_t s);
+void launch_check_range(const int32_t *a, int64_t n, int64_t hi, u64 *err, cudaStream_t s);
+void launch_sigma_from(int64_t n, const int32_t *C, const int64_t *K, int64_t *Sig,
+                       cudaStream_t s);
+
+// agg.cu: Alg. leidenag.  Input level graph g (nc communities in dense C);
+// output CSR (off2[nc+1], idx2, w2); returns nnz via ctr[CTR_SCRATCH0].
+struct AggWork {
+  int64_t *ccount, *coff, *ctdeg, *hoff, *cdist, *off2tmp;
+  int64_t *ccur;
+  int32_t *cv, *clist;
+  int32_t *hidx;
+  int64_t *hw;
+  int32_t *gkeys;
+  u64 *gvals;
+  int64_t gcap;
+  int32_t *blockhist;
+  int64_t *scanned;
+  int64_t *koff_dev;
+  int64_t *scan_tmp;
+  int64_t *h_koff;       // pinned host, >= MAX_TIERS + 3 entries
+  int64_t *Kout;         // [nc] row sums of the super-vertex graph (its K')
+  u64 *ctr;
+  int sms;
+};
+template <typename WT>
+int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int32_t *idx2,
+              int64_t *w2, int64_t *nnz2, const AggWork &wk, cudaStream_t s);
+
+// ds.cu / batch.cu
+struct DsWork {
+  int64_t *cnt;      // [n+1]
+  int64_t *soff;     // [n+1]
+  int64_t *cur;      // [n]
+  int32_t *sdst;     // [2*ni]
+  int32_t *swt;      // [2*ni]
+  int64_t *scan_tmp;
+  uint8_t *dE, *dC;
+};
+void launch_mark_ds(int64_t n, const int64_t *off, const int32_t *idx, const int32_t *Cprev,
+                    const int64_t *K, const int64_t *Sig, int64_t A, int64_t p,
+                    int64_t nd, const int32_t *ds, const int32_t *dd,
+                    int64_t ni, const int32_t *is, const int32_t *id, const int32_t *iw,
+                    uint8_t *affected, const DsWork &wk, cudaStream_t s);
+
+struct BatchWork {
+  int64_t *cnt;      // [n+1] insert counts per row, then offsets
+  int64_t *ioff;     // [n+1]
+  int64_t *cur;      // [n]
+  int32_t *idst;     // [2*ni]
+  int32_t *iwt;      // [2*ni]
+  int32_t *imatch;   // [2*ni] entry index of an existing edge, or -1
+  int64_t *newdeg;   // [n+1]
+  uint8_t *delmark;  // [nnz]
+  int32_t *wadd;     // [nnz] merged insertion weight per existing entry
+  int64_t *scan_tmp;
+  u64 *err;
+};
+int apply_batch(int64_t n, const int64_t *off, const int32_t *idx, const int32_t *w,
+                int64_t nd, const int32_t *ds, const int32_t *dd, const int32_t *dw,
+                int64_t ni, const int32_t *is, const int32_t *id, const int32_t *iw,
+                int64_t *off_out, int32_t *idx_out, int32_t *w_out, int64_t cap_nnz,
+                int64_t *nnz_out, const BatchWork &wk, cudaStream_t s);
+
+}  // namespace lk

@@ -1,0 +1,465 @@
+// move.cu -- local-moving (Alg. leidenlm) and refinement (Alg. leidenre)
+// kernels for sm_103a.
+//
+// Every vertex of a (colour class, degree tier) bucket gets a group of lanes,
+// a block, or a block with a global-memory table (hub rows).  The group hashes
+// K_{i->c} = sum of w_ij over neighbours j != i with C'[j] = c into an
+// open-addressing table (scanCommunities / scanBounded), then takes the argmax
+// of the scaled delta-modularity of Eq. 2 over the table's keys other than its
+// own community d (ties to the smallest ID).  All sums are integers, so the
+// result does not depend on hashing order or thread timing.
+//
+// DET: decide kernels read a snapshot (nothing they read is written until the
+// sub-sweep's apply kernel runs) and append proposals; apply kernels commit
+// them.  ASYNC: the deciding group commits immediately with atomics, like the
+// paper's asynchronous CPU implementation (Sec. 4.7).
+#include <limits.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lk {
+
+template <typename ST>
+__device__ __forceinline__ bool better(ST sc, int32_t c, ST bsc, int32_t bc) {
+  return c != INT32_MAX && (bc == INT32_MAX || sc > bsc || (sc == bsc && c < bc));
+}
+
+// Insert (c, w) into an open-addressing table of 2^log2H slots; the table has
+// at least twice as many slots as the row has entries, so it never fills.
+// Probing is bounded all the same: a full table sets *err and drops the entry.
+__device__ __forceinline__ void table_add(int32_t *keys, u64 *vals, int log2H, int32_t c, u64 w, u64 *err) {
+  const uint32_t mask = (1u << log2H) - 1u;
+  uint32_t s = hash32(c) >> (32 - log2H);
+  for (uint32_t probe = 0; probe <= mask; probe++) {
+    int32_t k = *(volatile int32_t *)&keys[s];
+    if (k == c) { atomicAdd(&vals[s], w); return; }
+    if (k == LEIDEN_EMPTY_KEY) {
+      int32_t old = atomicCAS(&keys[s], LEIDEN_EMPTY_KEY, c);
+      if (old == LEIDEN_EMPTY_KEY || old == c) { atomicAdd(&vals[s], w); return; }
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(err, 16ull);
+}
+
+// Eligibility of vertex i, decided by one thread.
+template <bool REFINE, typename WT>
+__device__ __forceinline__ bool eligible(const MoveArgs<WT> &a, int32_t i) {
+  if (!REFINE) {
+    if (a.processed[i]) return false;
+    a.processed[i] = 1;                                  // prune
+    return a.in_range ? a.in_range[i] != 0 : true;       // inAffectedRange
+  } else {
+    // reading: the flag of i's bound; i is still isolated iff Sigma'[i] = K'[i]
+    return a.changed[a.CB[i]] && a.C[i] == i && a.Sig[i] == a.K[i];
+  }
+}
+
+// Commit of an ASYNC move by one thread (the paper's in-place update).
+template <bool REFINE, typename WT>
+__device__ __forceinline__ bool commit_async(const MoveArgs<WT> &a, int32_t i, int32_t d,
+                                             int32_t c) {
+  const int64_t Ki = a.K[i];
+  if (!REFINE) {
+    atomic_add_i64(&a.Sig[d], -Ki);
+    atomic_add_i64(&a.Sig[c], Ki);
+    a.C[i] = c;
+    if (a.dynamic) { a.changed[d] = 1; a.changed[c] = 1; }
+    return true;
+  } else {
+    // atomicCAS(Sigma'[i], K'[i], 0) keeps i isolated until it leaves
+    u64 old = atomicCAS((u64 *)&a.Sig[i], (u64)Ki, 0ull);
+    if ((int64_t)old != Ki) return false;
+    atomic_add_i64(&a.Sig[c], Ki);
+    a.C[i] = c;
+    return true;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Group tier: G lanes and 2^LOG2H shared slots per vertex.
+// ---------------------------------------------------------------------------
+template <int G, int LOG2H, bool REFINE, bool ASYNC, typename WT, typename ST>
+__global__ void decide_group(MoveArgs<WT> a) {
+  constexpr int H = 1 << LOG2H;
+  constexpr int GPW = 32 / G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = lane / G, gl = lane % G;
+  const int leader = gw * G;
+  u64 *vals = reinterpret_cast<u64 *>(smem) + (size_t)(warp * GPW + gw) * H;
+  int32_t *keys = reinterpret_cast<int32_t *>(reinterpret_cast<u64 *>(smem) + (size_t)wpb * GPW * H) +
+                  (size_t)(warp * GPW + gw) * H;
+
+  int64_t scanned = 0, nvert = 0, ncand = 0, nmoves = 0;
+  i128 accS = 0;
+  const int64_t wglob = (int64_t)blockIdx.x * wpb + warp;
+  const int64_t nw = (int64_t)gridDim.x * wpb;
+  for (int64_t wb = wglob * GPW; wb < a.list_n; wb += nw * GPW) {
+    const int64_t li = wb + gw;
+    const bool valid = li < a.list_n;
+    int32_t i = valid ? a.list[li] : 0;
+    bool act = false;
+    if (gl == 0 && valid) act = eligible<REFINE>(a, i);
+    act = __shfl_sync(FULL_MASK, act, leader);
+    if (act) {
+      for (int s = gl; s < H; s += G) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
+    }
+    __syncwarp();
+    int32_t d = 0;
+    int64_t e0 = 0, e1 = 0;
+    if (act) {
+      d = a.C[i];
+      e0 = a.g.off[i];
+      e1 = a.g.off[i + 1];
+      const int32_t cbi = REFINE ? a.CB[i] : 0;
+      for (int64_t e = e0 + gl; e < e1; e += G) {
+        const int32_t j = a.g.idx[e];
+        if (j == i) continue;                           // self = false
+        if ((uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); continue; }
+        if (REFINE && a.CB[j] != cbi) continue;         // scanBounded
+        table_add(keys, vals, LOG2H, a.C[j], (u64)(int64_t)a.g.w[e], &a.ctr[CTR_ERROR]);
+      }
+      if (gl == 0) { scanned += e1 - e0; nvert++; }
+    }
+    __syncwarp();
+    ST bsc = 0;
+    int32_t bc = INT32_MAX;
+    int64_t kid = 0;
+    if (act) {
+      const ST A = (ST)a.A;
+      const ST B = (ST)a.p * (ST)a.K[i];
+      for (int s = gl; s < H; s += G) {
+        const int32_t c = keys[s];
+        if (c == LEIDEN_EMPTY_KEY) continue;
+        ncand++;
+        const int64_t v = (int64_t)vals[s];
+        if (c == d) { kid = v; continue; }
+        const ST sc = A * (ST)v - B * (ST)a.Sig[c];
+        if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
+      }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const ST osc = shfl_xor_any<ST>(bsc, o);
+      const int32_t oc = __shfl_xor_sync(FULL_MASK, bc, o);
+      kid += shfl_xor_i64(kid, o);
+      if (better(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
+    }
+    bool propose = false;
+    i128 S = 0;
+    if (act && gl == 0 && bc != INT32_MAX) {
+      const int64_t Ki = a.K[i];
+      S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - a.Sig[d]);
+      propose = S > 0;                                   // strictly better only
+      if (REFINE && propose && a.C[bc] != bc) propose = false;  // target's vertex left
+    }
+    if (ASYNC) {
+      if (propose) {
+        propose = commit_async<REFINE>(a, i, d, bc);
+        if (propose) { accS += S; nmoves++; }
+      }
+      if (!REFINE) {
+        const bool mv = __shfl_sync(FULL_MASK, propose, leader);
+        if (mv)
+          for (int64_t e = e0 + gl; e < e1; e += G) a.processed[a.g.idx[e]] = 0;
+      }
+    } else {
+      const u64 slot = warp_reserve(a.prop_count, propose);
+      if (propose) {
+        a.prop_i[slot] = i;
+        a.prop_c[slot] = bc;
+        a.prop_S[slot] = S;
+        if (REFINE) a.stamp[i] = a.stamp_val;
+      }
+    }
+    __syncwarp();
+  }
+  // counters
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    scanned += shfl_xor_i64(scanned, o);
+    nvert += shfl_xor_i64(nvert, o);
+    ncand += shfl_xor_i64(ncand, o);
+    nmoves += shfl_xor_i64(nmoves, o);
+    if (ASYNC) accS += shfl_xor_i128(accS, o);
+  }
+  if (lane == 0) {
+    if (scanned) atomicAdd(&a.ctr[CTR_SCANNED_ENTRIES], (u64)scanned);
+    if (nvert) atomicAdd(&a.ctr[CTR_SCANNED_VERTICES], (u64)nvert);
+    if (ncand) atomicAdd(&a.ctr[CTR_CANDIDATES], (u64)ncand);
+    if (ASYNC && nmoves) {
+      atomicAdd(&a.ctr[CTR_MOVES], (u64)nmoves);
+      atomic_add_i128(&a.ctr[CTR_SUMS_LO], accS);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block tiers: one block per vertex; table in shared memory (GLOBAL = false)
+// or in this block's slice of global scratch (GLOBAL = true, hub rows).
+// ---------------------------------------------------------------------------
+template <bool GLOBAL, bool REFINE, bool ASYNC, typename WT, typename ST>
+__global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int32_t s_i, s_d, s_act;
+  __shared__ int64_t s_e0, s_e1;
+  __shared__ ST r_sc[32];
+  __shared__ int32_t r_c[32];
+  __shared__ int64_t r_kid[32];
+  __shared__ int32_t s_mv;
+  const int Hmax = 1 << log2H;
+  u64 *vals;
+  int32_t *keys;
+  if (GLOBAL) {
+    vals = a.gvals + (size_t)blockIdx.x * Hmax;
+    keys = a.gkeys + (size_t)blockIdx.x * Hmax;
+  } else {
+    vals = reinterpret_cast<u64 *>(smem);
+    keys = reinterpret_cast<int32_t *>(vals + Hmax);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  int64_t scanned = 0, nvert = 0, ncand = 0, nmoves = 0;
+  i128 accS = 0;
+  for (int64_t li = blockIdx.x; li < a.list_n; li += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int32_t i = a.list[li];
+      const bool act = eligible<REFINE>(a, i);
+      s_i = i;
+      s_act = act;
+      if (act) { s_d = a.C[i]; s_e0 = a.g.off[i]; s_e1 = a.g.off[i + 1]; }
+    }
+    __syncthreads();
+    if (!s_act) { __syncthreads(); continue; }
+    const int32_t i = s_i, d = s_d;
+    const int64_t e0 = s_e0, e1 = s_e1;
+    // table sized for this row: at least 2 * degree slots, at most the tier's
+    int lh = 1;
+    while (lh < log2H && ((int64_t)1 << lh) < 2 * (e1 - e0)) lh++;
+    const int H = 1 << lh;
+    for (int s = threadIdx.x; s < H; s += blockDim.x) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
+    __syncthreads();
+    const int32_t cbi = REFINE ? a.CB[i] : 0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int32_t j = a.g.idx[e];
+      if (j == i) continue;
+      if ((uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); continue; }
+      if (REFINE && a.CB[j] != cbi) continue;
+      table_add(keys, vals, lh, a.C[j], (u64)(int64_t)a.g.w[e], &a.ctr[CTR_ERROR]);
+    }
+    if (threadIdx.x == 0) { scanned += e1 - e0; nvert++; }
+    __syncthreads();
+    const ST A = (ST)a.A;
+    const ST B = (ST)a.p * (ST)a.K[i];
+    ST bsc = 0;
+    int32_t bc = INT32_MAX;
+    int64_t kid = 0;
+    for (int s = threadIdx.x; s < H; s += blockDim.x) {
+      const int32_t c = keys[s];
+      if (c == LEIDEN_EMPTY_KEY) continue;
+      ncand++;
+      const int64_t v = (int64_t)vals[s];
+      if (c == d) { kid = v; continue; }
+      const ST sc = A * (ST)v - B * (ST)a.Sig[c];
+      if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const ST osc = shfl_xor_any<ST>(bsc, o);
+      const int32_t oc = __shfl_xor_sync(FULL_MASK, bc, o);
+      kid += shfl_xor_i64(kid, o);
+      if (better(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
+    }
+    if (lane == 0) { r_sc[warp] = bsc; r_c[warp] = bc; r_kid[warp] = kid; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 1; k < nwarp; k++) {
+        kid += r_kid[k];
+        if (better(r_sc[k], r_c[k], bsc, bc)) { bsc = r_sc[k]; bc = r_c[k]; }
+      }
+      bool propose = false;
+      i128 S = 0;
+      if (bc != INT32_MAX) {
+        const int64_t Ki = a.K[i];
+        S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - a.Sig[d]);
+        propose = S > 0;
+        if (REFINE && propose && a.C[bc] != bc) propose = false;
+      }
+      if (ASYNC) {
+        if (propose) propose = commit_async<REFINE>(a, i, d, bc);
+        if (propose) { accS += S; nmoves++; }
+      } else if (propose) {
+        const u64 slot = atomicAdd(a.prop_count, 1ull);
+        a.prop_i[slot] = i;
+        a.prop_c[slot] = bc;
+        a.prop_S[slot] = S;
+        if (REFINE) a.stamp[i] = a.stamp_val;
+      }
+      s_mv = propose;
+    }
+    __syncthreads();
+    if (ASYNC && !REFINE && s_mv)
+      for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) a.processed[a.g.idx[e]] = 0;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    scanned += shfl_xor_i64(scanned, o);
+    nvert += shfl_xor_i64(nvert, o);
+    ncand += shfl_xor_i64(ncand, o);
+  }
+  if (lane == 0) {
+    if (scanned) atomicAdd(&a.ctr[CTR_SCANNED_ENTRIES], (u64)scanned);
+    if (nvert) atomicAdd(&a.ctr[CTR_SCANNED_VERTICES], (u64)nvert);
+    if (ncand) atomicAdd(&a.ctr[CTR_CANDIDATES], (u64)ncand);
+  }
+  if (ASYNC && threadIdx.x == 0 && nmoves) {
+    atomicAdd(&a.ctr[CTR_MOVES], (u64)nmoves);
+    atomic_add_i128(&a.ctr[CTR_SUMS_LO], accS);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// DET apply kernels.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) apply_moves_k(const int32_t *prop_i, const int32_t *prop_c,
+                                                     const i128 *prop_S, u64 *ctr, int32_t *C,
+                                                     const int64_t *K, int64_t *Sig, uint8_t *changed,
+                                                     uint8_t *processed, const int64_t *off,
+                                                     const int32_t *idx, int dynamic) {
+  __shared__ i128 sbuf[32];
+  const u64 cnt = ctr[CTR_PROPS];
+  const int lane = threadIdx.x & 31;
+  const u64 wglob = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
+  i128 acc = 0;
+  for (u64 m = wglob; m < cnt; m += nw) {
+    const int32_t i = prop_i[m], c = prop_c[m];
+    if (lane == 0) {
+      const int32_t d = C[i];
+      const int64_t Ki = K[i];
+      atomic_add_i64(&Sig[d], -Ki);
+      atomic_add_i64(&Sig[c], Ki);
+      C[i] = c;
+      if (dynamic) { changed[d] = 1; changed[c] = 1; }
+      acc += prop_S[m];
+    }
+    // vertex pruning: a mover re-marks its neighbours
+    for (int64_t e = off[i] + lane; e < off[i + 1]; e += 32) processed[idx[e]] = 0;
+  }
+  const i128 tot = block_sum_i128(acc, sbuf);
+  if (threadIdx.x == 0 && tot != 0) atomic_add_i128(&ctr[CTR_SUMS_LO], tot);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctr[CTR_MOVES], cnt);
+}
+
+__global__ void __launch_bounds__(256) apply_refine_k(const int32_t *prop_i, const int32_t *prop_c,
+                                                      u64 *ctr, const uint8_t *stamp, uint8_t sv,
+                                                      int32_t *C, const int64_t *K, int64_t *Sig) {
+  const u64 cnt = ctr[CTR_PROPS];
+  u64 moved = 0;
+  for (u64 m = (u64)blockIdx.x * blockDim.x + threadIdx.x; m < cnt; m += (u64)gridDim.x * blockDim.x) {
+    const int32_t i = prop_i[m], c = prop_c[m];
+    if (stamp[c] == sv) continue;   // the target proposed to leave in this sub-sweep
+    const int64_t Ki = K[i];
+    atomic_add_i64(&Sig[i], -Ki);   // C'[i] = i: Sigma'[i] drops to 0
+    atomic_add_i64(&Sig[c], Ki);
+    C[i] = c;
+    moved++;
+  }
+  for (int o = 16; o > 0; o >>= 1) moved += __shfl_xor_sync(FULL_MASK, moved, o);
+  if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&ctr[CTR_MOVES], moved);
+}
+
+void launch_apply_moves(const int32_t *prop_i, const int32_t *prop_c, const i128 *prop_S,
+                        u64 *ctr, int32_t *C, const int64_t *K, int64_t *Sig,
+                        uint8_t *changed, uint8_t *processed, const int64_t *off,
+                        const int32_t *idx, int dynamic, int sms, cudaStream_t s) {
+  apply_moves_k<<<sms * 4, 256, 0, s>>>(prop_i, prop_c, prop_S, ctr, C, K, Sig, changed,
+                                        processed, off, idx, dynamic);
+}
+
+void launch_apply_refine(const int32_t *prop_i, const int32_t *prop_c, u64 *ctr,
+                         const uint8_t *stamp, uint8_t sv, int32_t *C, const int64_t *K,
+                         int64_t *Sig, int sms, cudaStream_t s) {
+  apply_refine_k<<<sms * 2, 256, 0, s>>>(prop_i, prop_c, ctr, stamp, sv, C, K, Sig);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+template <int G, int LOG2H, bool REFINE, bool ASYNC, typename WT, typename ST>
+static void launch_group_k(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s) {
+  auto k = decide_group<G, LOG2H, REFINE, ASYNC, WT, ST>;
+  const int threads = t.threads;
+  const size_t smem = (size_t)(threads / 32) * (32 / G) * (1u << LOG2H) * (sizeof(u64) + sizeof(int32_t));
+  if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t groups_per_block = (threads / 32) * (32 / G);
+  int64_t blocks = (a.list_n + groups_per_block - 1) / groups_per_block;
+  const int64_t cap = (int64_t)sms * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k<<<(unsigned)blocks, threads, smem, s>>>(a);
+}
+
+template <typename WT, typename ST, bool REFINE, bool ASYNC>
+void launch_decide(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s) {
+  if (a.list_n <= 0) return;
+  if (t.kind == TIER_GROUP) {
+#define LK_GROUP(GG, LH)                                                        \
+  if (t.G == GG && t.log2H == LH) {                                             \
+    launch_group_k<GG, LH, REFINE, ASYNC, WT, ST>(t, a, sms, s);                \
+    return;                                                                     \
+  }
+    LK_GROUP(4, 3) LK_GROUP(4, 4) LK_GROUP(8, 4) LK_GROUP(8, 5) LK_GROUP(16, 5) LK_GROUP(16, 6)
+    LK_GROUP(32, 6) LK_GROUP(32, 7) LK_GROUP(32, 8) LK_GROUP(32, 9) LK_GROUP(32, 10)
+#undef LK_GROUP
+    return;  // unsupported combination: the tier table is validated on the host
+  }
+  const bool global = t.kind == TIER_GLOBAL;
+  const int log2H = global ? a.glog2H : t.log2H;
+  const size_t smem = global ? 0 : (size_t)(1u << log2H) * (sizeof(u64) + sizeof(int32_t));
+  int64_t blocks = a.list_n;
+  const int64_t cap = global ? (int64_t)a.gblocks : (int64_t)sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) return;
+  if (global) {
+    auto k = decide_block<true, REFINE, ASYNC, WT, ST>;
+    k<<<(unsigned)blocks, t.threads, 0, s>>>(a, log2H);
+  } else {
+    auto k = decide_block<false, REFINE, ASYNC, WT, ST>;
+    if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<(unsigned)blocks, t.threads, smem, s>>>(a, log2H);
+  }
+}
+
+#define LK_INST(WT, ST)                                                                          \
+  template void launch_decide<WT, ST, false, false>(const Tier &, const MoveArgs<WT> &, int, cudaStream_t); \
+  template void launch_decide<WT, ST, true, false>(const Tier &, const MoveArgs<WT> &, int, cudaStream_t);  \
+  template void launch_decide<WT, ST, false, true>(const Tier &, const MoveArgs<WT> &, int, cudaStream_t);  \
+  template void launch_decide<WT, ST, true, true>(const Tier &, const MoveArgs<WT> &, int, cudaStream_t);
+LK_INST(int32_t, int64_t)
+LK_INST(int32_t, i128)
+LK_INST(int64_t, int64_t)
+LK_INST(int64_t, i128)
+#undef LK_INST
+
+TierTable default_tiers() {
+  TierTable tt{};
+  int k = 0;
+  tt.t[k++] = {TIER_SKIP, 0, 0, 0, 0};
+  tt.t[k++] = {TIER_GROUP, 4, 4, 3, 256};
+  tt.t[k++] = {TIER_GROUP, 8, 8, 4, 256};
+  tt.t[k++] = {TIER_GROUP, 16, 16, 5, 256};
+  tt.t[k++] = {TIER_GROUP, 32, 32, 6, 256};
+  tt.t[k++] = {TIER_GROUP, 128, 32, 8, 256};
+  tt.t[k++] = {TIER_GROUP, 512, 32, 10, 128};
+  tt.t[k++] = {TIER_BLOCK, 2048, 0, 12, 256};
+  tt.t[k++] = {TIER_BLOCK, 8192, 0, 14, 512};
+  tt.t[k++] = {TIER_GLOBAL, INT64_MAX, 0, 0, 1024};
+  tt.ntiers = k;
+  return tt;
+}
+
+}  // namespace lk

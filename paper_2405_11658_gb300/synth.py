@@ -203,21 +203,25 @@ def erdos_renyi(n: int, p: float, seed: int, wmax: int = 1):
     return edges_to_csr(n, iu[keep], ju[keep], w)
 
 
-def random_batch(off, idx, w, size: int, seed: int, ins_frac: float = 0.8, weight: int = 1):
+def random_batch(off, idx, w, size: int, seed: int, ins_frac: float = 0.8, weight: int = 1,
+                 pairs=None):
     """A batch of ``size`` undirected updates: round(ins_frac*size) insertions
     between uniformly chosen vertex pairs (self-loops, existing edges and
     repeats resampled) and the rest deletions of distinct, uniformly chosen
-    existing edges.  Returns (dels, ins), each (src, dst, w) int32 arrays."""
+    existing edges.  Returns (dels, ins), each (src, dst, w) int32 arrays.
+    ``pairs`` may pass a precomputed ``undirected_pairs(off, idx, w)``."""
     rng = _rng(seed)
     off = np.asarray(off, np.int64)
     n = len(off) - 1
-    eu, ev, ew = undirected_pairs(off, idx, w)
+    eu, ev, ew = pairs if pairs is not None else undirected_pairs(off, idx, w)
     ni = int(round(ins_frac * size))
     nd = min(size - ni, len(eu))
     pick = rng.choice(len(eu), size=nd, replace=False) if nd else np.zeros(0, np.int64)
     dels = (eu[pick].astype(np.int32), ev[pick].astype(np.int32),
             np.asarray(ew)[pick].astype(np.int32))
-    existing = np.sort(eu * n + ev)
+    existing = eu * n + ev
+    if len(existing) > 1 and not np.all(existing[1:] > existing[:-1]):
+        existing = np.sort(existing)
     got = np.zeros(0, np.int64)
     while len(got) < ni and n > 1:
         need = (ni - len(got)) * 2 + 8

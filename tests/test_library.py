@@ -1,0 +1,56 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for
+sm_103a, loads, and exports every function that include/leiden.h declares."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(leiden_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("leiden_static", "leiden_update", "leiden_modularity", "leiden_apply_batch",
+                     "leiden_ctx_create", "leiden_ctx_destroy"):
+        assert required in names
+
+
+def test_library_builds_loads_and_exports_every_symbol():
+    from paper_2405_11658_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_2405_11658_gb300 as L
+    monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(L, "_lib", None)
+    from paper_2405_11658_gb300 import build
+    monkeypatch.setattr(build, "build", lambda *a, **k: (_ for _ in ()).throw(RuntimeError("no nvcc")))
+    with pytest.raises(Exception):
+        L.lib()
+
+
+def test_strerror_and_defaults_without_gpu():
+    import paper_2405_11658_gb300 as L
+    d = L.default_opts()
+    assert d["gamma"] == 1.0 and d["tol"] == 0.01 and d["tol_drop"] == 10.0
+    assert d["max_iters"] == 20 and d["det_subsets"] == 8
+    assert L._strerror(-1) == "invalid argument"
