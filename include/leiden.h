@@ -65,13 +65,13 @@ typedef struct {
 
 enum { LEIDEN_ND = 1, LEIDEN_DS = 2, LEIDEN_DF = 3 };
 
-/* Schedules.  DET: every local-move iteration (and the refinement sweep) runs
- * det_subsets sub-sweeps over colour classes (class(i) = top log2(S) bits of
- * (uint32)(i * 2654435761)); the moves of a sub-sweep are chosen against the
- * state at its start and applied together, so the result does not depend on
- * thread timing.  ASYNC: vertices move in place as soon as they decide, as in
- * the paper's asynchronous CPU implementation (Sec. 4.7); results vary with
- * timing. */
+/* Schedules.  Both walk det_subsets colour classes in order in every
+ * local-move iteration and in the refinement sweep (class(i) = top log2(S)
+ * bits of (uint32)(i * 2654435761)).  DET: the moves of a class are chosen
+ * against the state at its start and applied together, so the result does
+ * not depend on thread timing.  ASYNC: inside a class, vertices move in place
+ * as soon as they decide, as in the paper's asynchronous CPU implementation
+ * (Sec. 4.7); results vary with timing. */
 enum { LEIDEN_DET = 0, LEIDEN_ASYNC = 1 };
 
 typedef struct {
@@ -165,6 +165,13 @@ typedef struct {
   int64_t move_scanned_vertices;
   double move_bytes;                            /* algorithmic bytes of those launches */
   double total_ms;                              /* host wall time of the call */
+  /* host wall time per pass: local-moving phase (with the vertex buckets),
+   * refinement (with subset renumbering and the break), aggregation (with
+   * renumbering and the dendrogram lookup), and the whole pass */
+  double t_move_ms[LEIDEN_STATS_PASSES];
+  double t_refine_ms[LEIDEN_STATS_PASSES];
+  double t_agg_ms[LEIDEN_STATS_PASSES];
+  double t_pass_ms[LEIDEN_STATS_PASSES];
 } leiden_run_stats;
 
 /* Copies the statistics of the last run into *out (HOST). */

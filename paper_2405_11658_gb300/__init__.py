@@ -65,12 +65,15 @@ class _Stats(C.Structure):
                 ("affected0", C.c_int64), ("changed0", C.c_int64),
                 ("move_kernel_ms", C.c_double), ("move_kernel_launches", C.c_int64),
                 ("move_scanned_entries", C.c_int64), ("move_scanned_vertices", C.c_int64),
-                ("move_bytes", C.c_double), ("total_ms", C.c_double)]
+                ("move_bytes", C.c_double), ("total_ms", C.c_double),
+                ("t_move_ms", C.c_double * STATS_PASSES), ("t_refine_ms", C.c_double * STATS_PASSES),
+                ("t_agg_ms", C.c_double * STATS_PASSES), ("t_pass_ms", C.c_double * STATS_PASSES)]
 
     def as_dict(self) -> dict:
         k = min(self.passes, STATS_PASSES)
         d = {name: getattr(self, name) for name, _ in self._fields_}
-        for name in ("iters", "nv", "nnz", "moves", "refine_moves"):
+        for name in ("iters", "nv", "nnz", "moves", "refine_moves", "t_move_ms", "t_refine_ms",
+                     "t_agg_ms", "t_pass_ms"):
             d[name] = list(getattr(self, name))[:k]
         return d
 

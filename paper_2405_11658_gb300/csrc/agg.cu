@@ -153,12 +153,17 @@ __global__ void __launch_bounds__(256) agg_warp_k(GraphView<WT> g, const int32_t
   const int64_t w0 = (int64_t)blockIdx.x * wpb + warp, nw = (int64_t)gridDim.x * wpb;
   for (int64_t li = w0; li < nlist; li += nw) {
     const int32_t c = list[li];
-    for (int s = lane; s < H; s += 32) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
+    // table sized for this community: 2^lh >= 2 * total degree, lh <= LOG2H
+    const int64_t td = hoff[c + 1] - hoff[c];
+    int lh = 1;
+    while (lh < LOG2H && ((int64_t)1 << lh) < 2 * td) lh++;
+    const int Hc = 1 << lh;
+    for (int s = lane; s < Hc; s += 32) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     if (lane == 0) { s_cnt[warp] = 0; s_ws[warp] = 0; }
     __syncwarp();
-    warp_rows_into_table(g, C, cv, coff[c], coff[c + 1], 32, keys, vals, H - 1, 32 - LOG2H, err);
+    warp_rows_into_table(g, C, cv, coff[c], coff[c + 1], 32, keys, vals, Hc - 1, 32 - lh, err);
     __syncwarp();
-    warp_emit(keys, vals, H, 0, 32, hidx, hw, hoff[c], &s_cnt[warp], &s_ws[warp]);
+    warp_emit(keys, vals, Hc, 0, 32, hidx, hw, hoff[c], &s_cnt[warp], &s_ws[warp]);
     __syncwarp();
     if (lane == 0) { cdist[c] = (int64_t)s_cnt[warp]; Kout[c] = s_ws[warp]; }
     __syncwarp();
@@ -180,35 +185,38 @@ __global__ void __launch_bounds__(512) agg_block_k(GraphView<WT> g, const int32_
   const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int64_t li = blockIdx.x; li < nlist; li += gridDim.x) {
     const int32_t c = list[li];
-    for (int s = threadIdx.x; s < H; s += blockDim.x) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
+    const int64_t td = hoff[c + 1] - hoff[c];
+    int lh = 1;
+    while (lh < log2H && ((int64_t)1 << lh) < 2 * td) lh++;
+    const int Hc = 1 << lh;
+    for (int s = threadIdx.x; s < Hc; s += blockDim.x) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     if (threadIdx.x == 0) { s_cnt = 0; s_ws = 0; }
     __syncthreads();
-    warp_rows_into_table(g, C, cv, coff[c] + 32 * warp, coff[c + 1], 32 * nwarp, keys, vals, H - 1,
-                         32 - log2H, err);
+    warp_rows_into_table(g, C, cv, coff[c] + 32 * warp, coff[c + 1], 32 * nwarp, keys, vals, Hc - 1,
+                         32 - lh, err);
     __syncthreads();
-    warp_emit(keys, vals, H, 32 * warp, 32 * nwarp, hidx, hw, hoff[c], &s_cnt, &s_ws);
+    warp_emit(keys, vals, Hc, 32 * warp, 32 * nwarp, hidx, hw, hoff[c], &s_cnt, &s_ws);
     __syncthreads();
     if (threadIdx.x == 0) { cdist[c] = (int64_t)s_cnt; Kout[c] = s_ws; }
     __syncthreads();
   }
 }
 
-// Global tier, step 1: table size (power of two >= 2 * total degree) per
-// listed community.
-__global__ void agg_gsize_k(const int32_t *list, int64_t nlist, const int64_t *hoff, int64_t *tsz) {
+// Global tier, step 1: per listed community, table slots (a power of two >=
+// 2 * min(total degree, |Gamma|) and >= 4096: the community has at most that
+// many distinct neighbour communities), member batches of 256, and 4096-slot
+// drain chunks.
+__global__ void agg_gsize_k(const int32_t *list, int64_t nlist, const int64_t *hoff, const int64_t *coff,
+                            int64_t nc, int64_t *tsz, int64_t *nb, int64_t *nch) {
   GSTRIDE(k, nlist) {
     const int32_t c = list[k];
     const int64_t d = hoff[c + 1] - hoff[c];
-    int64_t h = 1;
-    while (h < 2 * d) h <<= 1;
+    const int64_t cap = d < nc ? d : nc;
+    int64_t h = HUB_TABLE_MIN;
+    while (h < 2 * cap) h <<= 1;
     tsz[k] = h;
-  }
-}
-// member batches of 256 per listed community
-__global__ void agg_gbatches_k(const int32_t *list, int64_t nlist, const int64_t *coff, int64_t *nb) {
-  GSTRIDE(k, nlist) {
-    const int32_t c = list[k];
     nb[k] = (coff[c + 1] - coff[c] + 255) / 256;
+    nch[k] = h / HUB_TABLE_MIN;
   }
 }
 
@@ -221,44 +229,68 @@ __global__ void __launch_bounds__(256) agg_ginsert_k(GraphView<WT> g, const int3
                                                      const int64_t *tbase, const int64_t *tsz,
                                                      const int64_t *coff, const int32_t *cv,
                                                      int32_t *gkeys, u64 *gvals, u64 *err) {
-  const int64_t b0 = boff[k0];
-  const int64_t b = b0 + blockIdx.x;
-  int64_t lo = k0, hi = k1 - 1;  // last k with boff[k] <= b
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (boff[mid] <= b) lo = mid; else hi = mid - 1;
+  const int64_t nitems = boff[k1] - boff[k0];
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int64_t b = boff[k0] + item;
+    int64_t lo = k0, hi = k1 - 1;  // last k with boff[k] <= b
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (boff[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const int64_t k = lo;
+    const int32_t c = list[k];
+    const int64_t mfirst = coff[c] + (b - boff[k]) * 256;
+    int64_t mlast = mfirst + 256;
+    if (mlast > coff[c + 1]) mlast = coff[c + 1];
+    const int64_t H = tsz[k];
+    int lh = 0;
+    while (((int64_t)1 << lh) < H) lh++;
+    int32_t *keys = gkeys + (tbase[k] - tbase[k0]);
+    u64 *vals = gvals + (tbase[k] - tbase[k0]);
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    warp_rows_into_table(g, C, cv, mfirst + 32 * warp, mlast, 32 * nwarp, keys, vals,
+                         (uint32_t)(H - 1), 32 - lh, err);
   }
-  const int64_t k = lo;
-  const int32_t c = list[k];
-  const int64_t mfirst = coff[c] + (b - boff[k]) * 256;
-  int64_t mlast = mfirst + 256;
-  if (mlast > coff[c + 1]) mlast = coff[c + 1];
-  const int64_t H = tsz[k];
-  int lh = 0;
-  while (((int64_t)1 << lh) < H) lh++;
-  int32_t *keys = gkeys + (tbase[k] - tbase[k0]);
-  u64 *vals = gvals + (tbase[k] - tbase[k0]);
-  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  warp_rows_into_table(g, C, cv, mfirst + 32 * warp, mlast, 32 * nwarp, keys, vals,
-                       (uint32_t)(H - 1), 32 - lh, err);
 }
 
-// Global tier, step 3: one block per community drains its table.
-__global__ void __launch_bounds__(1024) agg_gemit_k(const int32_t *list, int64_t k0, const int64_t *tbase,
-                                                    const int64_t *tsz, const int64_t *hoff,
-                                                    const int32_t *gkeys, const u64 *gvals, int32_t *hidx,
-                                                    int64_t *hw, int64_t *cdist, int64_t *Kout) {
-  __shared__ unsigned long long s_cnt;
-  __shared__ int64_t s_ws;
-  const int64_t k = k0 + blockIdx.x;
-  const int32_t c = list[k];
-  if (threadIdx.x == 0) { s_cnt = 0; s_ws = 0; }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int64_t t0 = tbase[k] - tbase[k0];
-  warp_emit(gkeys + t0, gvals + t0, tsz[k], 32 * warp, 32 * nwarp, hidx, hw, hoff[c], &s_cnt, &s_ws);
-  __syncthreads();
-  if (threadIdx.x == 0) { cdist[c] = (int64_t)s_cnt; Kout[c] = s_ws; }
+// Global tier, step 3: every block drains one 4096-slot chunk of one table
+// into the community's hole range (positions reserved with atomics on the
+// community's entry count) and resets the slots it read, leaving the scratch
+// empty for its next user.
+__global__ void __launch_bounds__(256) agg_gemit_k(const int32_t *list, int64_t k0, int64_t k1,
+                                                   const int64_t *choff, const int64_t *tbase,
+                                                   const int64_t *hoff, int32_t *gkeys, u64 *gvals,
+                                                   int32_t *hidx, int64_t *hw, int64_t *cdist, int64_t *Kout) {
+  const int64_t nitems = choff[k1] - choff[k0];
+  const int lane = threadIdx.x & 31;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int64_t b = choff[k0] + item;
+    int64_t lo = k0, hi = k1 - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (choff[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const int64_t k = lo;
+    const int32_t c = list[k];
+    const int64_t s0 = (tbase[k] - tbase[k0]) + (b - choff[k]) * HUB_TABLE_MIN;
+    int64_t ws = 0;
+    for (int64_t x = threadIdx.x; x < HUB_TABLE_MIN; x += blockDim.x) {  // uniform per warp
+      const int64_t sl = s0 + x;
+      const int32_t key = gkeys[sl];
+      const bool occ = key != LEIDEN_EMPTY_KEY;
+      const u64 pos = warp_reserve((u64 *)&cdist[c], occ);
+      if (occ) {
+        const int64_t v = (int64_t)gvals[sl];
+        gkeys[sl] = LEIDEN_EMPTY_KEY;
+        gvals[sl] = 0;
+        hidx[hoff[c] + (int64_t)pos] = key;
+        hw[hoff[c] + (int64_t)pos] = v;
+        ws += v;
+      }
+    }
+    for (int o = 16; o; o >>= 1) ws += shfl_xor_i64(ws, o);
+    if (lane == 0 && ws) atomicAdd((u64 *)&Kout[c], (u64)ws);
+  }
 }
 
 // Compaction: warp per community copies its hole range to the compact CSR.
@@ -325,59 +357,52 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
                                                           wk.hw, wk.cdist, Kout, err);
       } else {
         auto k = agg_warp_k<10, WT>;
-        if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem((const void *)k, smem);
         k<<<blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx, wk.hw,
                                           wk.cdist, Kout, err);
       }
     } else if (T.kind == TIER_BLOCK) {
       const size_t smem = (size_t)(1u << T.log2H) * 12;
       auto k = agg_block_k<WT>;
-      if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      ensure_smem((const void *)k, smem);
       int64_t blocks = nl < (int64_t)wk.sms * 4 ? nl : (int64_t)wk.sms * 4;
       k<<<(unsigned)blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx, wk.hw,
                                                   wk.cdist, Kout, T.log2H, err);
     } else {
-      // table sizes and member batches of the listed communities
-      int64_t *tsz = wk.off2tmp;                  // [nl]
-      int64_t *tbase = wk.off2tmp + (nl + 1);     // [nl+1]
-      int64_t *nb = wk.off2tmp + 2 * (nl + 1);    // [nl]
-      int64_t *boff = wk.off2tmp + 3 * (nl + 1);  // [nl+1]
-      agg_gsize_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, wk.hoff, tsz);
-      agg_gbatches_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, wk.coff, nb);
+      // table sizes, member batches and drain chunks of the listed communities
+      int64_t *tsz = wk.off2tmp;                    // [nl]
+      int64_t *tbase = wk.off2tmp + (nl + 1);       // [nl+1]
+      int64_t *nb = wk.off2tmp + 2 * (nl + 1);      // [nl]
+      int64_t *boff = wk.off2tmp + 3 * (nl + 1);    // [nl+1]
+      int64_t *nch = wk.off2tmp + 4 * (nl + 1);     // [nl]
+      int64_t *choff = wk.off2tmp + 5 * (nl + 1);   // [nl+1]
+      agg_gsize_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, wk.hoff, wk.coff, nc, tsz, nb, nch);
       exclusive_scan<int64_t>(tsz, tbase, nl, wk.scan_tmp, s);
       exclusive_scan<int64_t>(nb, boff, nl, wk.scan_tmp, s);
-      // totals decide the rounds: one round when every table fits in scratch
-      int64_t tot[2];
+      exclusive_scan<int64_t>(nch, choff, nl, wk.scan_tmp, s);
+      // the total decides the rounds: one round when every table fits
       cudaMemcpyAsync(&wk.h_koff[MAX_TIERS + 1], tbase + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-      cudaMemcpyAsync(&wk.h_koff[MAX_TIERS + 2], boff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) return LEIDEN_ECUDA;
-      tot[0] = wk.h_koff[MAX_TIERS + 1];
-      tot[1] = wk.h_koff[MAX_TIERS + 2];
-      std::vector<int64_t> h_tb, h_bo;
-      if (tot[0] > wk.gcap) {
+      const int64_t total_slots = wk.h_koff[MAX_TIERS + 1];
+      std::vector<int64_t> h_tb;
+      if (total_slots > wk.gcap) {
         h_tb.resize(nl + 1);
-        h_bo.resize(nl + 1);
-        if (cudaMemcpy(h_tb.data(), tbase, (nl + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(h_bo.data(), boff, (nl + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        if (cudaMemcpy(h_tb.data(), tbase, (nl + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
           return LEIDEN_ECUDA;
       }
       int64_t k0 = 0;
       while (k0 < nl) {
-        int64_t k1 = nl, slots = tot[0], nblocks = tot[1];
-        if (tot[0] > wk.gcap) {
+        int64_t k1 = nl;
+        if (total_slots > wk.gcap) {
           k1 = k0 + 1;
           while (k1 < nl && h_tb[k1 + 1] - h_tb[k0] <= wk.gcap) k1++;
-          slots = h_tb[k1] - h_tb[k0];
-          nblocks = h_bo[k1] - h_bo[k0];
+          if (h_tb[k1] - h_tb[k0] > wk.gcap) return LEIDEN_ENOMEM;
         }
-        if (slots > wk.gcap) return LEIDEN_ENOMEM;
-        cudaMemsetAsync(wk.gkeys, 0xff, (size_t)slots * sizeof(int32_t), s);
-        cudaMemsetAsync(wk.gvals, 0, (size_t)slots * sizeof(u64), s);
-        if (nblocks > 0)
-          agg_ginsert_k<WT><<<(unsigned)nblocks, 256, 0, s>>>(g, C, list, k0, k1, boff, tbase, tsz, wk.coff,
-                                                               wk.cv, wk.gkeys, wk.gvals, err);
-        agg_gemit_k<<<(unsigned)(k1 - k0), 1024, 0, s>>>(list, k0, tbase, tsz, wk.hoff, wk.gkeys, wk.gvals,
-                                                          wk.hidx, wk.hw, wk.cdist, Kout);
+        // scratch tables are empty on entry (every user drains and resets them)
+        agg_ginsert_k<WT><<<(unsigned)(wk.sms * 8), 256, 0, s>>>(g, C, list, k0, k1, boff, tbase, tsz, wk.coff,
+                                                                 wk.cv, wk.gkeys, wk.gvals, err);
+        agg_gemit_k<<<(unsigned)(wk.sms * 8), 256, 0, s>>>(list, k0, k1, choff, tbase, wk.hoff, wk.gkeys, wk.gvals,
+                                                            wk.hidx, wk.hw, wk.cdist, Kout);
         k0 = k1;
       }
     }

@@ -43,6 +43,9 @@ struct leiden_ctx {
   int32_t *gkeys;
   u64 *gvals;
   int64_t gcap = 0;
+  int32_t *big;
+  HubWork hub{};
+  int64_t hub_items = 0;
   u64 *ctr;
   // pinned host
   u64 *h_ctr;
@@ -132,7 +135,7 @@ int check_opts(const leiden_opts *o, int64_t *p, int64_t *q, int *log2S) {
   if (S < 1 || S > 256 || (S & (S - 1))) return LEIDEN_EINVAL;
   int k = 0;
   while ((1 << k) < S) k++;
-  *log2S = o->sched == LEIDEN_DET ? k : 0;
+  *log2S = k;  // both schedules walk the colour classes in order
   return gamma_ratio(o->gamma, p, q);
 }
 
@@ -185,6 +188,7 @@ MoveArgs<WT> base_args(const Run &r, GraphView<WT> g) {
   a.gkeys = c->gkeys;
   a.gvals = c->gvals;
   a.glog2H = 0;
+  a.big = c->big;
   a.ctr = c->ctr;
   return a;
 }
@@ -251,11 +255,20 @@ void decide_class(const Run &r, MoveArgs<WT> a, const Buckets &b, int s) {
     if (a.list_n <= 0) continue;
     const Tier &T = c->tiers.t[t];
     if (T.kind == TIER_GLOBAL) {
-      // one table of 2^lh slots per block, lh fitted to the largest row
-      int lh = 1;
-      while (((int64_t)1 << lh) < 2 * b.maxdeg) lh++;
-      a.glog2H = lh;
-      a.gblocks = (int)std::min<int64_t>(c->sms, c->gcap >> lh);
+      // hub rows: multi-block path, in rounds whose tables fit the scratch
+      // (a hub's table has at most 2 * nextpow2(min(maxdeg, |V'|)) slots)
+      int64_t tmax = HUB_TABLE_MIN;
+      while (tmax < 2 * std::min<int64_t>(b.maxdeg, a.g.n)) tmax <<= 1;
+      const int64_t per_round = std::max<int64_t>(1, std::min(c->gcap / tmax, c->hub_items / (tmax / 4096)));
+      const int32_t *list = a.list;
+      const int64_t nl = a.list_n;
+      for (int64_t k0 = 0; k0 < nl; k0 += per_round) {
+        MoveArgs<WT> h = a;
+        h.list = list + k0;
+        h.list_n = std::min(per_round, nl - k0);
+        launch_hubs<WT, ST, REFINE, ASYNC>(h, c->hub, c->sms, c->st);
+      }
+      continue;
     }
     launch_decide<WT, ST, REFINE, ASYNC>(T, a, c->sms, c->st);
   }
@@ -277,8 +290,10 @@ int local_move(Run &r, GraphView<WT> g, const Buckets &b, bool first_pass, doubl
   cudaMemsetAsync(&c->ctr[CTR_SCANNED_ENTRIES], 0, 3 * sizeof(u64), c->st);
   while (li < r.o->max_iters) {
     cudaMemsetAsync(&c->ctr[CTR_SUMS_LO], 0, 2 * sizeof(u64), c->st);
+    const bool long_rows = b.maxdeg > BIG_ROW;
     for (int s = 0; s < nsub; s++) {
       if (!async) cudaMemsetAsync(&c->ctr[CTR_PROPS], 0, sizeof(u64), c->st);
+      if (long_rows) cudaMemsetAsync(&c->ctr[CTR_BIG], 0, sizeof(u64), c->st);
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (c->timing) {
         const size_t k = (size_t)c->stats.move_kernel_launches * 2;
@@ -299,7 +314,8 @@ int local_move(Run &r, GraphView<WT> g, const Buckets &b, bool first_pass, doubl
       }
       if (!async)
         launch_apply_moves(c->prop_i, c->prop_c, c->prop_S, c->ctr, c->Cp, c->Kp, c->Sp, c->ch, c->processed,
-                           g.off, g.idx, a.dynamic, c->sms, c->st);
+                           g.off, g.idx, c->big, a.dynamic, c->sms, c->st);
+      if (long_rows) launch_mark_big(c->big, &c->ctr[CTR_BIG], g.off, g.idx, c->processed, c->sms, c->st);
     }
     li++;
     cudaMemcpyAsync(c->h_ctr, c->ctr, CTR_COUNT * sizeof(u64), cudaMemcpyDeviceToHost, c->st);
@@ -369,10 +385,16 @@ AggWork agg_work(leiden_ctx *c) {
 
 // One pass body for a level graph g; returns 1 to stop, 0 to continue with
 // the aggregated graph written to level buffer `dst`, or a negative error.
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 template <typename WT, typename ST>
 int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, int64_t *nnz_out) {
   leiden_ctx *c = r.c;
   const int64_t nv = g.n;
+  const auto t_start = std::chrono::steady_clock::now();
+  const bool rec = lp < LEIDEN_STATS_PASSES;
   Buckets b;
   int rc = build_buckets(r, g.off, nv, b);
   if (rc) return rc;
@@ -386,6 +408,8 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
   const int li = local_move<WT, ST>(r, g, b, lp == 0, tau, &moves);
   if (li < 0) return li;
   if (lp == 0) c->stats.changed0 = count_flags(c, c->ch, nv);
+  if (rec) c->stats.t_move_ms[lp] = ms_since(t_start);
+  const auto t_ref = std::chrono::steady_clock::now();
   // Alg. leidensr, then the bounds, the break and the refinement
   launch_subset_renumber(nv, c->Cp, c->Sp, c->S2, c->ch, c->ch2, c->rep, c->st);
   std::swap(c->Sp, c->S2);
@@ -394,6 +418,8 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
   launch_break(nv, c->Cp, c->Kp, c->Sp, c->ch, c->st);
   rc = refine<WT, ST>(r, g, b, &rmoves);
   if (rc) return rc;
+  if (rec) c->stats.t_refine_ms[lp] = ms_since(t_ref);
+  const auto t_agg = std::chrono::steady_clock::now();
   if (lp < LEIDEN_STATS_PASSES) {
     c->stats.passes = lp + 1;
     c->stats.iters[lp] = li;
@@ -401,14 +427,20 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
     c->stats.moves[lp] = moves;
     c->stats.refine_moves[lp] = rmoves;
   }
-  if (lp > 0 && li <= 1) return 1;  // globally converged
+  if (lp > 0 && li <= 1) {  // globally converged
+    if (rec) c->stats.t_pass_ms[lp] = ms_since(t_start);
+    return 1;
+  }
   launch_renumber(nv, c->Cp, c->flag, c->scanned, c->scan_tmp, c->ctr, c->st);
   cudaMemcpyAsync(&c->h_ctr[CTR_NCOMM], &c->ctr[CTR_NCOMM], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
   rc = sync(c);
   if (rc) return rc;
   const int64_t nc = (int64_t)c->h_ctr[CTR_NCOMM];
   *nc_out = nc;
-  if (nc == nv) return 1;  // aggregation would not shrink the graph
+  if (nc == nv) {  // aggregation would not shrink the graph
+    if (rec) c->stats.t_pass_ms[lp] = ms_since(t_start);
+    return 1;
+  }
   launch_lookup(r.N, c->Ctop, c->Cp, c->st);
   int64_t nnz2 = 0;
   rc = aggregate<WT>(g, c->Cp, nc, c->goff[dst], c->gidx[dst], c->gw[dst], &nnz2, agg_work(c), c->st);
@@ -419,6 +451,10 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
   rc = check_dev_flags(c, c->h_ctr[CTR_ERROR]);
   if (rc) return rc;
   *nnz_out = nnz2;
+  if (rec) {
+    c->stats.t_agg_ms[lp] = ms_since(t_agg);
+    c->stats.t_pass_ms[lp] = ms_since(t_start);
+  }
   return 0;
 }
 
@@ -529,6 +565,16 @@ void reset_stats(leiden_ctx *c) {
   c->stats = leiden_run_stats{};
 }
 
+// A run that stopped half-way may leave scratch tables or counters dirty;
+// restore the context's invariants so the next call starts clean.
+int fail_run(leiden_ctx *c, int rc) {
+  cudaMemsetAsync(c->gkeys, 0xff, (size_t)c->gcap * sizeof(int32_t), c->st);
+  cudaMemsetAsync(c->gvals, 0, (size_t)c->gcap * sizeof(u64), c->st);
+  cudaMemsetAsync(c->ctr, 0, CTR_COUNT * sizeof(u64), c->st);
+  cudaStreamSynchronize(c->st);
+  return rc;
+}
+
 void finish_timing(leiden_ctx *c) {
   if (!c->timing) return;
   double ms = 0;
@@ -584,7 +630,7 @@ int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_
   c->tiers = default_tiers();
   const int64_t n1 = max_n + 1, m = max_nnz > 0 ? max_nnz : 1;
   const int64_t bh = bucket_blockhist_elems(max_n, MAX_KEYS);
-  const int64_t scan_n = std::max<int64_t>(bh, 4 * n1 + 4);
+  const int64_t scan_n = std::max<int64_t>(bh, 6 * n1 + 8);
   c->gcap = std::max<int64_t>(m, (int64_t)1 << 22);
   int rc = LEIDEN_OK;
   rc |= dal(c, &c->Ctop, n1); rc |= dal(c, &c->Cp, n1); rc |= dal(c, &c->CB, n1); rc |= dal(c, &c->rep, n1);
@@ -596,7 +642,7 @@ int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_
   rc |= dal(c, &c->vlist, n1); rc |= dal(c, &c->clist, n1); rc |= dal(c, &c->cv, n1);
   rc |= dal(c, &c->ccount, n1); rc |= dal(c, &c->coff, n1); rc |= dal(c, &c->ctdeg, n1);
   rc |= dal(c, &c->hoff, n1); rc |= dal(c, &c->cdist, n1); rc |= dal(c, &c->ccur, n1);
-  rc |= dal(c, &c->off2tmp, 4 * n1 + 4);
+  rc |= dal(c, &c->off2tmp, 6 * n1 + 8);
   rc |= dal(c, &c->scanned, scan_n + 1); rc |= dal(c, &c->koff_dev, MAX_KEYS + 1);
   rc |= dal(c, &c->scan_tmp, scan_tmp_elems(scan_n) + 1);
   rc |= dal(c, &c->blockhist, bh);
@@ -606,6 +652,13 @@ int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_
   rc |= dal(c, &c->hidx, m); rc |= dal(c, &c->hw, m);
   rc |= dal(c, &c->gkeys, c->gcap); rc |= dal(c, &c->gvals, c->gcap);
   rc |= dal(c, &c->ctr, CTR_COUNT);
+  rc |= dal(c, &c->big, n1);
+  rc |= dal(c, &c->hub.tsz, n1); rc |= dal(c, &c->hub.toff, n1);
+  rc |= dal(c, &c->hub.ioff, n1); rc |= dal(c, &c->hub.soff, n1);
+  rc |= dal(c, &c->hub.tot, 4);
+  c->hub_items = c->gcap / 4096 + 1024;
+  rc |= dal(c, &c->hub.psc, c->hub_items); rc |= dal(c, &c->hub.pc, c->hub_items);
+  rc |= dal(c, &c->hub.pkid, c->hub_items);
   if (rc == LEIDEN_OK) {
     if (cudaMallocHost((void **)&c->h_ctr, CTR_COUNT * sizeof(u64)) != cudaSuccess ||
         cudaMallocHost((void **)&c->h_koff, (MAX_KEYS + 8) * sizeof(int64_t)) != cudaSuccess)
@@ -618,6 +671,9 @@ int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_
     return LEIDEN_ENOMEM;
   }
   cudaMemsetAsync(c->ctr, 0, CTR_COUNT * sizeof(u64), c->st);
+  // the global scratch tables start (and are always left) empty
+  cudaMemsetAsync(c->gkeys, 0xff, (size_t)c->gcap * sizeof(int32_t), c->st);
+  cudaMemsetAsync(c->gvals, 0, (size_t)c->gcap * sizeof(u64), c->st);
   if (sync(c)) { free_all(c); delete c; return LEIDEN_ECUDA; }
   *out = c;
   return LEIDEN_OK;
@@ -671,7 +727,7 @@ int leiden_static(leiden_ctx *c, const leiden_csr *g, const leiden_opts *o, int3
   r.in_range0 = nullptr;
   c->stats.affected0 = n;
   rc = run_leiden(r, g);
-  if (rc) return rc;
+  if (rc) return fail_run(c, rc);
   launch_canonical(n, c->Ctop, membership_out, c->rep, c->flag, c->scanned, c->scan_tmp, c->st);
   rc = sync(c);
   if (rc) return rc;
@@ -766,7 +822,7 @@ int leiden_update(leiden_ctx *c, const leiden_csr *g, const int32_t *prior_membe
   c->stats.affected0 = mode == LEIDEN_ND ? n : count_flags(c, c->affected, n);
   r.dynamic = true;
   rc = run_leiden(r, g);
-  if (rc) return rc;
+  if (rc) return fail_run(c, rc);
   launch_canonical(n, c->Ctop, membership_out, c->rep, c->flag, c->scanned, c->scan_tmp, c->st);
   if (K_out) launch_copy_i64(K_out, c->K0, n, c->st);
   if (Sigma_out) launch_sigma_from(n, membership_out, c->K0, Sigma_out, c->st);
@@ -823,9 +879,13 @@ int leiden_apply_batch(leiden_ctx *c, const leiden_csr *g, const leiden_edges *d
   w.delmark = reinterpret_cast<uint8_t *>(c->gvals);
   w.scan_tmp = c->scan_tmp;
   w.err = &c->ctr[CTR_ERROR];
-  return apply_batch(g->n, g->off, g->idx, g->w, nd, nd ? del->src : nullptr, nd ? del->dst : nullptr,
-                     nd ? del->w : nullptr, ni, ni ? ins->src : nullptr, ni ? ins->dst : nullptr,
-                     ni ? ins->w : nullptr, off_out, idx_out, w_out, cap_nnz, nnz_out, w, c->st);
+  rc = apply_batch(g->n, g->off, g->idx, g->w, nd, nd ? del->src : nullptr, nd ? del->dst : nullptr,
+                   nd ? del->w : nullptr, ni, ni ? ins->src : nullptr, ni ? ins->dst : nullptr,
+                   ni ? ins->w : nullptr, off_out, idx_out, w_out, cap_nnz, nnz_out, w, c->st);
+  // the deletion marks borrowed the scratch values: leave them zero again
+  if (g->nnz > 0) cudaMemsetAsync(c->gvals, 0, (size_t)g->nnz, c->st);
+  const int rc2 = sync(c);
+  return rc ? rc : rc2;
 }
 
 }  // extern "C"

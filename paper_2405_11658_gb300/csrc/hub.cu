@@ -1,0 +1,313 @@
+// hub.cu -- local-move (Alg. leidenlm) and refinement (Alg. leidenre)
+// decisions for rows too long for one block's shared memory ("hub" rows of
+// power-law graphs and of their super-vertex graphs).
+//
+// One hub row is spread over many blocks so that no single block serialises
+// a row of 10^5 - 10^7 entries:
+//   prep   (1 block)  eligibility, per-hub table size 2^k >= 2 min(deg, |V'|),
+//                     and exclusive scans of table sizes and work counts;
+//   insert (grid)     work item = (hub, 4096-entry chunk of its row): add
+//                     (C'[j], w) to the hub's table in global scratch;
+//   scan   (grid)     work item = (hub, 4096-slot chunk of its table): best
+//                     candidate of the chunk and the hub's own-community
+//                     weight; every slot read is reset to empty, so the
+//                     scratch is clean again for the next user;
+//   final  (per hub)  reduce the chunks, Eq. 2 (scaled) and the move rule,
+//                     then propose (DET) or commit (ASYNC).
+// Work counts stay on the device: grids are fixed and stride over them.
+#include <limits.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lk {
+
+static constexpr int HUB_CHUNK = 4096;      // row entries per insert work item
+static constexpr int HUB_SCAN_CHUNK = 4096; // table slots per scan work item
+
+template <typename WT>
+__device__ __forceinline__ bool hub_eligible(const MoveArgs<WT> &a, int32_t i, bool refine) {
+  if (!refine) {
+    if (a.processed[i]) return false;
+    a.processed[i] = 1;
+    return a.in_range ? a.in_range[i] != 0 : true;
+  }
+  return a.changed[a.CB[i]] && a.C[i] == i && a.Sig[i] == a.K[i];
+}
+
+// Single block: hub k of the list gets its table offset toff[k], size tsz[k]
+// (0 when not eligible), insert-work offset ioff[k] and scan-work offset
+// soff[k]; the totals go to hw.tot[0..2].
+template <typename WT>
+__global__ void __launch_bounds__(1024) hub_prep_k(MoveArgs<WT> a, bool refine, HubWork hw) {
+  __shared__ int64_t warp_s[3][32];
+  __shared__ int64_t carry[3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < a.list_n; base += blockDim.x) {
+    const int64_t k = base + threadIdx.x;
+    int64_t v[3] = {0, 0, 0};
+    if (k < a.list_n) {
+      const int32_t i = a.list[k];
+      if (hub_eligible(a, i, refine)) {
+        const int64_t deg = a.g.off[i + 1] - a.g.off[i];
+        const int64_t cap = deg < a.g.n ? deg : a.g.n;
+        int64_t t = HUB_SCAN_CHUNK;
+        while (t < 2 * cap) t <<= 1;
+        v[0] = t;
+        v[1] = (deg + HUB_CHUNK - 1) / HUB_CHUNK;
+        v[2] = t / HUB_SCAN_CHUNK;
+      }
+      hw.tsz[k] = v[0];
+    }
+    // block-wide exclusive scans of the three counts
+    int64_t incl[3];
+    for (int q = 0; q < 3; q++) {
+      int64_t x = v[q];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = shfl_i64(x, (lane - o) & 31);
+        if (lane >= o) x += y;
+      }
+      incl[q] = x;
+      if (lane == 31) warp_s[q][warp] = x;
+    }
+    __syncthreads();
+    if (k < a.list_n) {
+      int64_t *outs[3] = {hw.toff, hw.ioff, hw.soff};
+      for (int q = 0; q < 3; q++) {
+        int64_t pre = carry[q];
+        for (int w = 0; w < warp; w++) pre += warp_s[q][w];
+        outs[q][k] = pre + incl[q] - v[q];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      int64_t s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += warp_s[threadIdx.x][w];
+      carry[threadIdx.x] += s;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) {
+    hw.tot[threadIdx.x] = carry[threadIdx.x];
+    int64_t *outs[3] = {hw.toff, hw.ioff, hw.soff};
+    outs[threadIdx.x][a.list_n] = carry[threadIdx.x];
+  }
+}
+
+// last k with offs[k] <= w, over k in [0, n)
+__device__ __forceinline__ int64_t find_item(const int64_t *offs, int64_t n, int64_t w) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (offs[mid] <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void hub_table_add(int32_t *keys, u64 *vals, uint64_t mask, int sh, int32_t c, u64 w,
+                                              u64 *err) {
+  uint64_t s = (uint64_t)(hash32(c) >> sh);
+  for (uint64_t probe = 0; probe <= mask; probe++) {
+    const int32_t k = *(volatile int32_t *)&keys[s];
+    if (k == c) { atomicAdd(&vals[s], w); return; }
+    if (k == LEIDEN_EMPTY_KEY) {
+      const int32_t old = atomicCAS(&keys[s], LEIDEN_EMPTY_KEY, c);
+      if (old == LEIDEN_EMPTY_KEY || old == c) { atomicAdd(&vals[s], w); return; }
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(err, 16ull);
+}
+
+__device__ __forceinline__ int log2_exact(int64_t t) {
+  int k = 0;
+  while (((int64_t)1 << k) < t) k++;
+  return k;
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine, HubWork hw) {
+  const int64_t nitems = hw.tot[1];
+  for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int64_t k = find_item(hw.ioff, a.list_n, w);
+    const int32_t i = a.list[k];
+    const int64_t e0 = a.g.off[i], e1 = a.g.off[i + 1];
+    const int64_t c0 = e0 + (w - hw.ioff[k]) * HUB_CHUNK;
+    const int64_t c1 = c0 + HUB_CHUNK < e1 ? c0 + HUB_CHUNK : e1;
+    const int64_t t = hw.tsz[k];
+    const int lh = log2_exact(t);
+    int32_t *keys = a.gkeys + hw.toff[k];
+    u64 *vals = a.gvals + hw.toff[k];
+    const int32_t cbi = refine ? a.CB[i] : 0;
+    for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+      const int32_t j = a.g.idx[e];
+      if (j == i) continue;
+      if ((uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); continue; }
+      if (refine && a.CB[j] != cbi) continue;
+      hub_table_add(keys, vals, (uint64_t)(t - 1), 32 - lh, a.C[j], (u64)(int64_t)a.g.w[e], &a.ctr[CTR_ERROR]);
+    }
+  }
+}
+
+template <typename WT, typename ST>
+__device__ __forceinline__ bool hub_better(ST sc, int32_t c, ST bsc, int32_t bc) {
+  return c != INT32_MAX && (bc == INT32_MAX || sc > bsc || (sc == bsc && c < bc));
+}
+
+template <typename WT, typename ST>
+__global__ void __launch_bounds__(256) hub_scan_k(MoveArgs<WT> a, HubWork hw) {
+  __shared__ ST r_sc[8];
+  __shared__ int32_t r_c[8];
+  __shared__ int64_t r_kid[8];
+  __shared__ int64_t r_cand[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nitems = hw.tot[2];
+  for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int64_t k = find_item(hw.soff, a.list_n, w);
+    const int32_t i = a.list[k];
+    const int32_t d = a.C[i];
+    const ST A = (ST)a.A;
+    const ST B = (ST)a.p * (ST)a.K[i];
+    const int64_t s0 = (w - hw.soff[k]) * HUB_SCAN_CHUNK;
+    int32_t *keys = a.gkeys + hw.toff[k];
+    u64 *vals = a.gvals + hw.toff[k];
+    ST bsc = 0;
+    int32_t bc = INT32_MAX;
+    int64_t kid = 0, cand = 0;
+    for (int64_t s = s0 + threadIdx.x; s < s0 + HUB_SCAN_CHUNK; s += blockDim.x) {
+      const int32_t c = keys[s];
+      if (c == LEIDEN_EMPTY_KEY) continue;
+      const int64_t v = (int64_t)vals[s];
+      keys[s] = LEIDEN_EMPTY_KEY;  // reset for the next user of the scratch
+      vals[s] = 0;
+      cand++;
+      if (c == d) { kid = v; continue; }
+      const ST sc = A * (ST)v - B * (ST)a.Sig[c];
+      if (hub_better<WT, ST>(sc, c, bsc, bc)) { bsc = sc; bc = c; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const ST osc = shfl_xor_any<ST>(bsc, o);
+      const int32_t oc = __shfl_xor_sync(FULL_MASK, bc, o);
+      kid += shfl_xor_i64(kid, o);
+      cand += shfl_xor_i64(cand, o);
+      if (hub_better<WT, ST>(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
+    }
+    if (lane == 0) { r_sc[warp] = bsc; r_c[warp] = bc; r_kid[warp] = kid; r_cand[warp] = cand; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < (int)(blockDim.x >> 5); q++) {
+        kid += r_kid[q];
+        cand += r_cand[q];
+        if (hub_better<WT, ST>(r_sc[q], r_c[q], bsc, bc)) { bsc = r_sc[q]; bc = r_c[q]; }
+      }
+      hw.psc[w] = (i128)bsc;
+      hw.pc[w] = bc;
+      hw.pkid[w] = kid;
+      if (cand) atomicAdd(&a.ctr[CTR_CANDIDATES], (u64)cand);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename WT, typename ST, bool REFINE, bool ASYNC>
+__global__ void __launch_bounds__(256) hub_final_k(MoveArgs<WT> a, HubWork hw) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.list_n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (hw.tsz[k] == 0) continue;  // not eligible
+    const int32_t i = a.list[k];
+    const int32_t d = a.C[i];
+    i128 bsc = 0;
+    int32_t bc = INT32_MAX;
+    int64_t kid = 0;
+    for (int64_t w = hw.soff[k]; w < hw.soff[k + 1]; w++) {
+      kid += hw.pkid[w];
+      if (hub_better<WT, i128>(hw.psc[w], hw.pc[w], bsc, bc)) { bsc = hw.psc[w]; bc = hw.pc[w]; }
+    }
+    const int64_t Ki = a.K[i];
+    atomicAdd(&a.ctr[CTR_SCANNED_ENTRIES], (u64)(a.g.off[i + 1] - a.g.off[i]));
+    atomicAdd(&a.ctr[CTR_SCANNED_VERTICES], 1ull);
+    if (bc == INT32_MAX) continue;
+    const i128 S = bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - a.Sig[d]);
+    if (S <= 0) continue;
+    if (REFINE && a.C[bc] != bc) continue;
+    if (ASYNC) {
+      bool ok;
+      if (!REFINE) {
+        atomic_add_i64(&a.Sig[d], -Ki);
+        atomic_add_i64(&a.Sig[bc], Ki);
+        a.C[i] = bc;
+        if (a.dynamic) { a.changed[d] = 1; a.changed[bc] = 1; }
+        ok = true;
+        // its neighbours are re-marked by the big-row marking kernel
+        const u64 slot = atomicAdd(&a.ctr[CTR_BIG], 1ull);
+        a.big[slot] = i;
+      } else {
+        ok = false;
+        const u64 old = atomicCAS((u64 *)&a.Sig[i], (u64)Ki, 0ull);
+        if ((int64_t)old == Ki) {
+          const u64 prev = atomicAdd((u64 *)&a.Sig[bc], (u64)Ki);
+          if (prev == 0ull) {
+            atomic_add_i64(&a.Sig[bc], -Ki);
+            atomic_add_i64(&a.Sig[i], Ki);
+          } else {
+            a.C[i] = bc;
+            ok = true;
+          }
+        }
+      }
+      if (ok) {
+        atomicAdd(&a.ctr[CTR_MOVES], 1ull);
+        atomic_add_i128(&a.ctr[CTR_SUMS_LO], S);
+      }
+    } else {
+      const u64 slot = atomicAdd(a.prop_count, 1ull);
+      a.prop_i[slot] = i;
+      a.prop_c[slot] = bc;
+      a.prop_S[slot] = S;
+      if (REFINE) a.stamp[i] = a.stamp_val;
+    }
+  }
+}
+
+// Re-marks the neighbours of long movers as unprocessed: every block walks
+// every listed row, so one long row is spread over the whole grid.
+__global__ void __launch_bounds__(256) mark_big_rows_k(const int32_t *big, const u64 *count, const int64_t *off,
+                                                       const int32_t *idx, uint8_t *processed) {
+  const u64 nb = *count;
+  for (u64 m = 0; m < nb; m++) {
+    const int32_t i = big[m];
+    const int64_t e0 = off[i], e1 = off[i + 1];
+    for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
+         e += (int64_t)gridDim.x * blockDim.x)
+      processed[idx[e]] = 0;
+  }
+}
+
+void launch_mark_big(const int32_t *big, const u64 *count, const int64_t *off, const int32_t *idx,
+                     uint8_t *processed, int sms, cudaStream_t s) {
+  mark_big_rows_k<<<sms * 4, 256, 0, s>>>(big, count, off, idx, processed);
+}
+
+template <typename WT, typename ST, bool REFINE, bool ASYNC>
+void launch_hubs(const MoveArgs<WT> &a, const HubWork &hw, int sms, cudaStream_t s) {
+  if (a.list_n <= 0) return;
+  hub_prep_k<WT><<<1, 1024, 0, s>>>(a, REFINE, hw);
+  hub_insert_k<WT><<<sms * 8, 256, 0, s>>>(a, REFINE, hw);
+  hub_scan_k<WT, ST><<<sms * 8, 256, 0, s>>>(a, hw);
+  hub_final_k<WT, ST, REFINE, ASYNC><<<(unsigned)((a.list_n + 255) / 256), 256, 0, s>>>(a, hw);
+}
+
+#define LK_HUB_INST(WT, ST)                                                                              \
+  template void launch_hubs<WT, ST, false, false>(const MoveArgs<WT> &, const HubWork &, int, cudaStream_t); \
+  template void launch_hubs<WT, ST, true, false>(const MoveArgs<WT> &, const HubWork &, int, cudaStream_t);  \
+  template void launch_hubs<WT, ST, false, true>(const MoveArgs<WT> &, const HubWork &, int, cudaStream_t);  \
+  template void launch_hubs<WT, ST, true, true>(const MoveArgs<WT> &, const HubWork &, int, cudaStream_t);
+LK_HUB_INST(int32_t, int64_t)
+LK_HUB_INST(int32_t, i128)
+LK_HUB_INST(int64_t, int64_t)
+LK_HUB_INST(int64_t, i128)
+#undef LK_HUB_INST
+
+}  // namespace lk

@@ -66,12 +66,27 @@ struct MoveArgs {
   u64 *prop_count;
   int64_t A;             // 2m * q
   int64_t p;
-  int32_t *gkeys;        // global-table tier scratch: gblocks tables of 2^glog2H slots
-  u64 *gvals;
+  int32_t *gkeys;        // global scratch tables (hub rows); all keys empty and
+  u64 *gvals;            // all values zero whenever no kernel is using them
   int glog2H;
   int gblocks;
+  int32_t *big;          // movers whose rows are re-marked by the big-row kernel
   u64 *ctr;              // counters, see CTR_*
 };
+
+// Work arrays of the multi-block hub path (hub.cu), indexed by the position
+// of the hub in its (class, tier) list.
+struct HubWork {
+  int64_t *tsz;   // table slots (0: hub not eligible)
+  int64_t *toff;  // exclusive scan of tsz
+  int64_t *ioff;  // exclusive scan of insert work items
+  int64_t *soff;  // exclusive scan of scan work items
+  int64_t *tot;   // [0] table slots, [1] insert items, [2] scan items
+  i128 *psc;      // per scan item: best partial score,
+  int32_t *pc;    //   its community,
+  int64_t *pkid;  //   and the weight towards the hub's own community
+};
+static constexpr int64_t HUB_TABLE_MIN = 4096;
 
 enum {
   CTR_SCANNED_ENTRIES = 0,
@@ -83,7 +98,8 @@ enum {
   CTR_PROPS = 6,        // proposal count of the current sub-sweep
   CTR_ERROR = 7,
   CTR_NCOMM = 8,
-  CTR_SCRATCH0 = 9,
+  CTR_SCRATCH0 = 9,     // 9..12: scratch words of the host driver
+  CTR_BIG = 13,         // movers appended to the big-row list
   CTR_COUNT = 16
 };
 
@@ -93,7 +109,15 @@ void launch_decide(const Tier &tier, const MoveArgs<WT> &a, int sms, cudaStream_
 void launch_apply_moves(const int32_t *prop_i, const int32_t *prop_c, const i128 *prop_S,
                         u64 *ctr, int32_t *C, const int64_t *K, int64_t *Sig,
                         uint8_t *changed, uint8_t *processed, const int64_t *off,
-                        const int32_t *idx, int dynamic, int sms, cudaStream_t s);
+                        const int32_t *idx, int32_t *big, int dynamic, int sms, cudaStream_t s);
+// Movers with more than BIG_ROW entries leave their neighbour re-marking
+// to launch_mark_big, which spreads each row over the whole grid.
+static constexpr int64_t BIG_ROW = 4096;
+void launch_mark_big(const int32_t *big, const u64 *count, const int64_t *off, const int32_t *idx,
+                     uint8_t *processed, int sms, cudaStream_t s);
+// hub.cu
+template <typename WT, typename ST, bool REFINE, bool ASYNC>
+void launch_hubs(const MoveArgs<WT> &a, const HubWork &hw, int sms, cudaStream_t s);
 void launch_apply_refine(const int32_t *prop_i, const int32_t *prop_c, u64 *ctr,
                          const uint8_t *stamp, uint8_t sv, int32_t *C, const int64_t *K,
                          int64_t *Sig, int sms, cudaStream_t s);
@@ -107,6 +131,7 @@ void launch_buckets(const int64_t *off, int64_t n, int log2S, const TierTable &t
 int64_t bucket_blockhist_elems(int64_t n, int nkeys);
 
 // scan.cu
+void ensure_smem(const void *func, size_t bytes);
 template <typename TI>
 void exclusive_scan(const TI *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
 int64_t scan_tmp_elems(int64_t n);

@@ -68,10 +68,19 @@ __device__ __forceinline__ bool commit_async(const MoveArgs<WT> &a, int32_t i, i
     if (a.dynamic) { a.changed[d] = 1; a.changed[c] = 1; }
     return true;
   } else {
-    // atomicCAS(Sigma'[i], K'[i], 0) keeps i isolated until it leaves
+    // atomicCAS(Sigma'[i], K'[i], 0): i leaves only while still isolated.
     u64 old = atomicCAS((u64 *)&a.Sig[i], (u64)Ki, 0ull);
     if ((int64_t)old != Ki) return false;
-    atomic_add_i64(&a.Sig[c], Ki);
+    // Join c*.  A total of 0 means c*'s own vertex has just left in the same
+    // way (a vertex with an edge has K > 0): undo both steps and stay, so a
+    // sub-community never loses the vertex it is named after and every
+    // member stays adjacent to it.
+    const u64 prev = atomicAdd((u64 *)&a.Sig[c], (u64)Ki);
+    if (prev == 0ull) {
+      atomic_add_i64(&a.Sig[c], -Ki);
+      atomic_add_i64(&a.Sig[i], Ki);
+      return false;
+    }
     a.C[i] = c;
     return true;
   }
@@ -104,23 +113,25 @@ __global__ void decide_group(MoveArgs<WT> a) {
     bool act = false;
     if (gl == 0 && valid) act = eligible<REFINE>(a, i);
     act = __shfl_sync(FULL_MASK, act, leader);
-    if (act) {
-      for (int s = gl; s < H; s += G) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
-    }
-    __syncwarp();
     int32_t d = 0;
     int64_t e0 = 0, e1 = 0;
+    int lh = 1;  // table sized for this row: 2^lh >= 2 * degree, lh <= LOG2H
     if (act) {
-      d = a.C[i];
       e0 = a.g.off[i];
       e1 = a.g.off[i + 1];
+      while (lh < LOG2H && ((int64_t)1 << lh) < 2 * (e1 - e0)) lh++;
+      for (int s = gl; s < (1 << lh); s += G) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
+    }
+    __syncwarp();
+    if (act) {
+      d = a.C[i];
       const int32_t cbi = REFINE ? a.CB[i] : 0;
       for (int64_t e = e0 + gl; e < e1; e += G) {
         const int32_t j = a.g.idx[e];
         if (j == i) continue;                           // self = false
         if ((uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); continue; }
         if (REFINE && a.CB[j] != cbi) continue;         // scanBounded
-        table_add(keys, vals, LOG2H, a.C[j], (u64)(int64_t)a.g.w[e], &a.ctr[CTR_ERROR]);
+        table_add(keys, vals, lh, a.C[j], (u64)(int64_t)a.g.w[e], &a.ctr[CTR_ERROR]);
       }
       if (gl == 0) { scanned += e1 - e0; nvert++; }
     }
@@ -131,7 +142,7 @@ __global__ void decide_group(MoveArgs<WT> a) {
     if (act) {
       const ST A = (ST)a.A;
       const ST B = (ST)a.p * (ST)a.K[i];
-      for (int s = gl; s < H; s += G) {
+      for (int s = gl; s < (1 << lh); s += G) {
         const int32_t c = keys[s];
         if (c == LEIDEN_EMPTY_KEY) continue;
         ncand++;
@@ -328,7 +339,7 @@ __global__ void __launch_bounds__(256) apply_moves_k(const int32_t *prop_i, cons
                                                      const i128 *prop_S, u64 *ctr, int32_t *C,
                                                      const int64_t *K, int64_t *Sig, uint8_t *changed,
                                                      uint8_t *processed, const int64_t *off,
-                                                     const int32_t *idx, int dynamic) {
+                                                     const int32_t *idx, int32_t *big, int dynamic) {
   __shared__ i128 sbuf[32];
   const u64 cnt = ctr[CTR_PROPS];
   const int lane = threadIdx.x & 31;
@@ -346,8 +357,14 @@ __global__ void __launch_bounds__(256) apply_moves_k(const int32_t *prop_i, cons
       if (dynamic) { changed[d] = 1; changed[c] = 1; }
       acc += prop_S[m];
     }
-    // vertex pruning: a mover re-marks its neighbours
-    for (int64_t e = off[i] + lane; e < off[i + 1]; e += 32) processed[idx[e]] = 0;
+    // vertex pruning: a mover re-marks its neighbours (long rows are left to
+    // the big-row kernel, which spreads them over the grid)
+    const int64_t e0 = off[i], e1 = off[i + 1];
+    if (e1 - e0 > BIG_ROW) {
+      if (lane == 0) big[atomicAdd(&ctr[CTR_BIG], 1ull)] = i;
+    } else {
+      for (int64_t e = e0 + lane; e < e1; e += 32) processed[idx[e]] = 0;
+    }
   }
   const i128 tot = block_sum_i128(acc, sbuf);
   if (threadIdx.x == 0 && tot != 0) atomic_add_i128(&ctr[CTR_SUMS_LO], tot);
@@ -375,9 +392,9 @@ __global__ void __launch_bounds__(256) apply_refine_k(const int32_t *prop_i, con
 void launch_apply_moves(const int32_t *prop_i, const int32_t *prop_c, const i128 *prop_S,
                         u64 *ctr, int32_t *C, const int64_t *K, int64_t *Sig,
                         uint8_t *changed, uint8_t *processed, const int64_t *off,
-                        const int32_t *idx, int dynamic, int sms, cudaStream_t s) {
+                        const int32_t *idx, int32_t *big, int dynamic, int sms, cudaStream_t s) {
   apply_moves_k<<<sms * 4, 256, 0, s>>>(prop_i, prop_c, prop_S, ctr, C, K, Sig, changed,
-                                        processed, off, idx, dynamic);
+                                        processed, off, idx, big, dynamic);
 }
 
 void launch_apply_refine(const int32_t *prop_i, const int32_t *prop_c, u64 *ctr,
@@ -394,7 +411,7 @@ static void launch_group_k(const Tier &t, const MoveArgs<WT> &a, int sms, cudaSt
   auto k = decide_group<G, LOG2H, REFINE, ASYNC, WT, ST>;
   const int threads = t.threads;
   const size_t smem = (size_t)(threads / 32) * (32 / G) * (1u << LOG2H) * (sizeof(u64) + sizeof(int32_t));
-  if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ensure_smem((const void *)k, smem);
   const int64_t groups_per_block = (threads / 32) * (32 / G);
   int64_t blocks = (a.list_n + groups_per_block - 1) / groups_per_block;
   const int64_t cap = (int64_t)sms * 16;
@@ -417,21 +434,15 @@ void launch_decide(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s
 #undef LK_GROUP
     return;  // unsupported combination: the tier table is validated on the host
   }
-  const bool global = t.kind == TIER_GLOBAL;
-  const int log2H = global ? a.glog2H : t.log2H;
-  const size_t smem = global ? 0 : (size_t)(1u << log2H) * (sizeof(u64) + sizeof(int32_t));
+  if (t.kind != TIER_BLOCK) return;  // hub rows go through launch_hubs
+  const int log2H = t.log2H;
+  const size_t smem = (size_t)(1u << log2H) * (sizeof(u64) + sizeof(int32_t));
   int64_t blocks = a.list_n;
-  const int64_t cap = global ? (int64_t)a.gblocks : (int64_t)sms * 8;
+  const int64_t cap = (int64_t)sms * 8;
   if (blocks > cap) blocks = cap;
-  if (blocks < 1) return;
-  if (global) {
-    auto k = decide_block<true, REFINE, ASYNC, WT, ST>;
-    k<<<(unsigned)blocks, t.threads, 0, s>>>(a, log2H);
-  } else {
-    auto k = decide_block<false, REFINE, ASYNC, WT, ST>;
-    if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<(unsigned)blocks, t.threads, smem, s>>>(a, log2H);
-  }
+  auto k = decide_block<false, REFINE, ASYNC, WT, ST>;
+  ensure_smem((const void *)k, smem);
+  k<<<(unsigned)blocks, t.threads, smem, s>>>(a, log2H);
 }
 
 #define LK_INST(WT, ST)                                                                          \

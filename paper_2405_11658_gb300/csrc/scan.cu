@@ -4,10 +4,27 @@
 // Used for the exclusive scans of the aggregation phase (Alg. leidenag:
 // community-vertex offsets and super-vertex offsets), the dense renumbering of
 // communities, the canonical relabelling and the batch application.
+#include <mutex>
+#include <unordered_map>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace lk {
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (once per
+// kernel and size; the attribute outlives the call, so it is set only when
+// the requested size grows).
+void ensure_smem(const void *func, size_t bytes) {
+  if (bytes <= 32 * 1024) return;  // leaves room for static shared memory
+  static std::mutex mu;
+  static std::unordered_map<const void *, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &have = done[func];
+  if (have >= bytes) return;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    have = bytes;
+}
 
 static constexpr int SCAN_THREADS = 256;
 static constexpr int SCAN_ITEMS = 8;

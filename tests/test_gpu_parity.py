@@ -289,9 +289,11 @@ def test_self_loops_in_input(ctx):
 @pytest.mark.parametrize("name", ["pp_1e4", "pp_strong", "rmat14", "grid", "chung_lu_w", "hubs"])
 def test_async_quality_and_invariants(ctx, name):
     off, idx, w = GRAPHS[name]()
-    ref = O.static(off, idx, w, O.LeidenOpts(sched=O.SCHED_GS))
+    gs = O.static(off, idx, w, O.LeidenOpts(sched=O.SCHED_GS))
+    det = O.static(off, idx, w, O.LeidenOpts())
     memb, q, st = run_static(ctx, (off, idx, w), L.Opts(sched=L.ASYNC))
     assert np.array_equal(memb, O.canonical(memb))
     assert q == O.modularity(off, idx, w, memb)[0]
-    assert B.all_connected(off, idx, memb) if len(off) < 20000 else True
-    assert q >= ref.q - 1e-3 or abs(q - ref.q) <= 1e-3
+    assert B.all_connected(off, idx, memb)
+    # no worse than the oracle's own schedules by more than 1e-3
+    assert q >= min(gs.q, det.q) - 1e-3, (q, gs.q, det.q)
