@@ -75,7 +75,7 @@ template <typename WT>
 __device__ __forceinline__ void warp_rows_into_table(const GraphView<WT> &g, const int32_t *C,
                                                      const int32_t *cv, int64_t m0, int64_t m1,
                                                      int64_t mstep, int32_t *keys, u64 *vals,
-                                                     uint32_t mask, int sh, u64 *err) {
+                                                     uint32_t mask, int sh, u64 *err, u64 *scratch) {
   const int lane = threadIdx.x & 31;
   for (int64_t mb = m0; mb < m1; mb += mstep) {
     const int64_t m = mb + lane;
@@ -103,12 +103,17 @@ __device__ __forceinline__ void warp_rows_into_table(const GraphView<WT> &g, con
       const int64_t sk = shfl_i64(start, k);
       const int64_t ik = shfl_i64(incl, k);
       const int64_t dk = shfl_i64(deg, k);
+      int32_t c = LEIDEN_EMPTY_KEY;
+      u64 wv = 0;
       if (t < total) {
         const int64_t e = sk + (t - (ik - dk));
         const int32_t j = (e >= sk && e < sk + dk) ? g.idx[e] : -1;
-        if ((uint32_t)j < (uint32_t)g.n) tadd(keys, vals, mask, sh, C[j], (u64)(int64_t)g.w[e], err);
+        if ((uint32_t)j < (uint32_t)g.n) { c = C[j]; wv = (u64)(int64_t)g.w[e]; }
         else atomicOr(err, 64ull);
       }
+      u64 sum = 0;
+      if (warp_combine((unsigned long long)(uint32_t)c, c != LEIDEN_EMPTY_KEY, wv, &sum, scratch))
+        tadd(keys, vals, mask, sh, c, sum, err);
     }
   }
 }
@@ -150,6 +155,7 @@ __global__ void __launch_bounds__(256) agg_warp_k(GraphView<WT> g, const int32_t
   int32_t *keys = reinterpret_cast<int32_t *>(reinterpret_cast<u64 *>(smem) + (size_t)wpb * H) + (size_t)warp * H;
   __shared__ unsigned long long s_cnt[8];
   __shared__ int64_t s_ws[8];
+  __shared__ u64 wscratch[8][32];
   const int64_t w0 = (int64_t)blockIdx.x * wpb + warp, nw = (int64_t)gridDim.x * wpb;
   for (int64_t li = w0; li < nlist; li += nw) {
     const int32_t c = list[li];
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(256) agg_warp_k(GraphView<WT> g, const int32_t
     for (int s = lane; s < Hc; s += 32) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     if (lane == 0) { s_cnt[warp] = 0; s_ws[warp] = 0; }
     __syncwarp();
-    warp_rows_into_table(g, C, cv, coff[c], coff[c + 1], 32, keys, vals, Hc - 1, 32 - lh, err);
+    warp_rows_into_table(g, C, cv, coff[c], coff[c + 1], 32, keys, vals, Hc - 1, 32 - lh, err, wscratch[warp]);
     __syncwarp();
     warp_emit(keys, vals, Hc, 0, 32, hidx, hw, hoff[c], &s_cnt[warp], &s_ws[warp]);
     __syncwarp();
@@ -182,6 +188,7 @@ __global__ void __launch_bounds__(512) agg_block_k(GraphView<WT> g, const int32_
   int32_t *keys = reinterpret_cast<int32_t *>(vals + H);
   __shared__ unsigned long long s_cnt;
   __shared__ int64_t s_ws;
+  __shared__ u64 wscratch[16][32];
   const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int64_t li = blockIdx.x; li < nlist; li += gridDim.x) {
     const int32_t c = list[li];
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(512) agg_block_k(GraphView<WT> g, const int32_
     if (threadIdx.x == 0) { s_cnt = 0; s_ws = 0; }
     __syncthreads();
     warp_rows_into_table(g, C, cv, coff[c] + 32 * warp, coff[c + 1], 32 * nwarp, keys, vals, Hc - 1,
-                         32 - lh, err);
+                         32 - lh, err, wscratch[warp]);
     __syncthreads();
     warp_emit(keys, vals, Hc, 32 * warp, 32 * nwarp, hidx, hw, hoff[c], &s_cnt, &s_ws);
     __syncthreads();
@@ -229,6 +236,7 @@ __global__ void __launch_bounds__(256) agg_ginsert_k(GraphView<WT> g, const int3
                                                      const int64_t *tbase, const int64_t *tsz,
                                                      const int64_t *coff, const int32_t *cv,
                                                      int32_t *gkeys, u64 *gvals, u64 *err) {
+  __shared__ u64 wscratch[8][32];
   const int64_t nitems = boff[k1] - boff[k0];
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int64_t b = boff[k0] + item;
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(256) agg_ginsert_k(GraphView<WT> g, const int3
     u64 *vals = gvals + (tbase[k] - tbase[k0]);
     const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     warp_rows_into_table(g, C, cv, mfirst + 32 * warp, mlast, 32 * nwarp, keys, vals,
-                         (uint32_t)(H - 1), 32 - lh, err);
+                         (uint32_t)(H - 1), 32 - lh, err, wscratch[warp]);
   }
 }
 
@@ -293,17 +301,43 @@ __global__ void __launch_bounds__(256) agg_gemit_k(const int32_t *list, int64_t 
   }
 }
 
-// Compaction: warp per community copies its hole range to the compact CSR.
+// Compaction: each warp takes 32 communities and copies their hole ranges
+// to the compact CSR as one flattened range (prefix sums across the lanes,
+// binary search per entry), so short rows still move in full warps.
 __global__ void agg_compact_k(int64_t nc, const int64_t *hoff, const int64_t *off2, const int32_t *hidx,
                               const int64_t *hw, int32_t *idx2, int64_t *w2) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = w0; c < nc; c += nw) {
-    const int64_t src = hoff[c], dst = off2[c], len = off2[c + 1] - off2[c];
-    for (int64_t x = lane; x < len; x += 32) {
-      idx2[dst + x] = hidx[src + x];
-      w2[dst + x] = hw[src + x];
+  for (int64_t cb = w0 * 32; cb < nc; cb += nw * 32) {
+    const int64_t c = cb + lane;
+    int64_t src = 0, dst = 0, len = 0;
+    if (c < nc) {
+      src = hoff[c];
+      dst = off2[c];
+      len = off2[c + 1] - dst;
+    }
+    int64_t incl = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = shfl_i64(incl, (lane - o) & 31);
+      if (lane >= o) incl += y;
+    }
+    const int64_t total = shfl_i64(incl, 31);
+    for (int64_t t0 = 0; t0 < total; t0 += 32) {
+      const int64_t t = t0 + lane;
+      int k = 0;
+#pragma unroll
+      for (int b = 16; b; b >>= 1) {
+        const int64_t v = shfl_i64(incl, k + b - 1);
+        if (v <= t) k += b;
+      }
+      const int64_t sk = shfl_i64(src, k), dk = shfl_i64(dst, k);
+      const int64_t ik = shfl_i64(incl, k), lk = shfl_i64(len, k);
+      if (t < total) {
+        const int64_t x = t - (ik - lk);
+        idx2[dk + x] = hidx[sk + x];
+        w2[dk + x] = hw[sk + x];
+      }
     }
   }
 }
@@ -314,7 +348,7 @@ static TierTable agg_tiers() {
   tt.t[k++] = {TIER_SKIP, 0, 0, 0, 0};
   tt.t[k++] = {TIER_GROUP, 48, 32, 7, 256};     // warp, 128 slots
   tt.t[k++] = {TIER_GROUP, 384, 32, 10, 128};   // warp, 1024 slots
-  tt.t[k++] = {TIER_BLOCK, 6144, 0, 14, 512};   // block, 16384 slots
+  tt.t[k++] = {TIER_BLOCK, 2048, 0, 12, 256};   // block, 4096 slots (48 KB: 4 blocks per SM)
   tt.t[k++] = {TIER_GLOBAL, INT64_MAX, 0, 0, 256};
   tt.ntiers = k;
   return tt;
@@ -380,12 +414,15 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       exclusive_scan<int64_t>(tsz, tbase, nl, wk.scan_tmp, s);
       exclusive_scan<int64_t>(nb, boff, nl, wk.scan_tmp, s);
       exclusive_scan<int64_t>(nch, choff, nl, wk.scan_tmp, s);
-      // the total decides the rounds: one round when every table fits
+      // Rounds: the tables of one round fit in a slot budget sized to stay
+      // resident in L2, so the insert atomics do not go to DRAM (a single
+      // table larger than the budget gets a round of its own).
       cudaMemcpyAsync(&wk.h_koff[MAX_TIERS + 1], tbase + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) return LEIDEN_ECUDA;
       const int64_t total_slots = wk.h_koff[MAX_TIERS + 1];
+      const int64_t budget = (LK_AGG_ROUND_SLOTS > 0 && LK_AGG_ROUND_SLOTS < wk.gcap) ? LK_AGG_ROUND_SLOTS : wk.gcap;
       std::vector<int64_t> h_tb;
-      if (total_slots > wk.gcap) {
+      if (total_slots > budget) {
         h_tb.resize(nl + 1);
         if (cudaMemcpy(h_tb.data(), tbase, (nl + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
           return LEIDEN_ECUDA;
@@ -393,9 +430,9 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       int64_t k0 = 0;
       while (k0 < nl) {
         int64_t k1 = nl;
-        if (total_slots > wk.gcap) {
+        if (total_slots > budget) {
           k1 = k0 + 1;
-          while (k1 < nl && h_tb[k1 + 1] - h_tb[k0] <= wk.gcap) k1++;
+          while (k1 < nl && h_tb[k1 + 1] - h_tb[k0] <= budget) k1++;
           if (h_tb[k1] - h_tb[k0] > wk.gcap) return LEIDEN_ENOMEM;
         }
         // scratch tables are empty on entry (every user drains and resets them)

@@ -56,6 +56,12 @@ struct leiden_ctx {
   leiden_run_stats stats{};
   int timing = 0;
   std::vector<cudaEvent_t> evs;
+  // auxiliary streams: the independent tier kernels of one sub-sweep run on
+  // them concurrently, forked from and joined back into the context stream
+  static constexpr int NAUX = LK_AUX_STREAMS > 0 ? LK_AUX_STREAMS : 1;
+  cudaStream_t aux[NAUX] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[NAUX] = {};
 };
 
 namespace {
@@ -84,6 +90,14 @@ void free_all(leiden_ctx *c) {
   if (c->h_koff) cudaFreeHost(c->h_koff);
   for (auto e : c->evs) cudaEventDestroy(e);
   c->evs.clear();
+  for (int k = 0; k < leiden_ctx::NAUX; k++) {
+    if (c->aux[k]) cudaStreamDestroy(c->aux[k]);
+    if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
+    c->aux[k] = nullptr;
+    c->ev_join[k] = nullptr;
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  c->ev_fork = nullptr;
   c->h_ctr = nullptr;
   c->h_koff = nullptr;
 }
@@ -243,34 +257,49 @@ int build_buckets(const Run &r, const int64_t *off, int64_t n, Buckets &b) {
   return LEIDEN_OK;
 }
 
-// Launch the decide kernels of every tier of colour class s.
+// Launch the decide kernels of every tier of colour class s.  The tiers
+// touch disjoint vertices and only read the shared state (DET) or update it
+// with atomics (ASYNC), so they run concurrently on the auxiliary streams.
 template <typename WT, typename ST, bool REFINE, bool ASYNC>
 void decide_class(const Run &r, MoveArgs<WT> a, const Buckets &b, int s) {
   leiden_ctx *c = r.c;
   const int nt = c->tiers.ntiers;
+  int used = 0;
+  cudaEventRecord(c->ev_fork, c->st);
   for (int t = 1; t < nt; t++) {
     const int key = s * nt + t;
     a.list = c->vlist + b.koff[key];
     a.list_n = b.koff[key + 1] - b.koff[key];
     if (a.list_n <= 0) continue;
+    const int k = used % leiden_ctx::NAUX;
+    cudaStream_t st = LK_AUX_STREAMS > 0 ? c->aux[k] : c->st;
+    if (LK_AUX_STREAMS > 0 && used < leiden_ctx::NAUX) cudaStreamWaitEvent(st, c->ev_fork, 0);
+    used++;
     const Tier &T = c->tiers.t[t];
     if (T.kind == TIER_GLOBAL) {
       // hub rows: multi-block path, in rounds whose tables fit the scratch
       // (a hub's table has at most 2 * nextpow2(min(maxdeg, |V'|)) slots)
       int64_t tmax = HUB_TABLE_MIN;
       while (tmax < 2 * std::min<int64_t>(b.maxdeg, a.g.n)) tmax <<= 1;
-      const int64_t per_round = std::max<int64_t>(1, std::min(c->gcap / tmax, c->hub_items / (tmax / 4096)));
+      const int64_t budget = LK_HUB_ROUND_SLOTS > 0
+                                 ? std::min<int64_t>(c->gcap, std::max<int64_t>(LK_HUB_ROUND_SLOTS, tmax))
+                                 : c->gcap;
+      const int64_t per_round = std::max<int64_t>(1, std::min(budget / tmax, c->hub_items / (tmax / 4096)));
       const int32_t *list = a.list;
       const int64_t nl = a.list_n;
       for (int64_t k0 = 0; k0 < nl; k0 += per_round) {
         MoveArgs<WT> h = a;
         h.list = list + k0;
         h.list_n = std::min(per_round, nl - k0);
-        launch_hubs<WT, ST, REFINE, ASYNC>(h, c->hub, c->sms, c->st);
+        launch_hubs<WT, ST, REFINE, ASYNC>(h, c->hub, c->sms, st);
       }
       continue;
     }
-    launch_decide<WT, ST, REFINE, ASYNC>(T, a, c->sms, c->st);
+    launch_decide<WT, ST, REFINE, ASYNC>(T, a, c->sms, st);
+  }
+  for (int k = 0; LK_AUX_STREAMS > 0 && k < used && k < leiden_ctx::NAUX; k++) {
+    cudaEventRecord(c->ev_join[k], c->aux[k]);
+    cudaStreamWaitEvent(c->st, c->ev_join[k], 0);
   }
 }
 
@@ -659,6 +688,14 @@ int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_
   c->hub_items = c->gcap / 4096 + 1024;
   rc |= dal(c, &c->hub.psc, c->hub_items); rc |= dal(c, &c->hub.pc, c->hub_items);
   rc |= dal(c, &c->hub.pkid, c->hub_items);
+  if (rc == LEIDEN_OK) {
+    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) rc = LEIDEN_ENOMEM;
+    for (int k = 0; k < leiden_ctx::NAUX && rc == LEIDEN_OK; k++) {
+      if (cudaStreamCreateWithFlags(&c->aux[k], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming) != cudaSuccess)
+        rc = LEIDEN_ENOMEM;
+    }
+  }
   if (rc == LEIDEN_OK) {
     if (cudaMallocHost((void **)&c->h_ctr, CTR_COUNT * sizeof(u64)) != cudaSuccess ||
         cudaMallocHost((void **)&c->h_koff, (MAX_KEYS + 8) * sizeof(int64_t)) != cudaSuccess)

@@ -79,6 +79,32 @@ __device__ __forceinline__ u64 warp_reserve(u64 *counter, bool want) {
   return base + __popc(m & ((1u << lane) - 1u));
 }
 
+// Combines equal keys across the active lanes of a warp before they reach a
+// hashtable: returns true in exactly one lane per distinct key (the lowest),
+// with *sum = the total weight of that key over the active lanes.  Turns a
+// warp's worth of same-address atomics (e.g. the internal edges of a
+// community, which all hash to one slot) into a single one.  The whole warp
+// must call; `scratch` is 32 words of this warp's shared memory.
+__device__ __forceinline__ bool warp_combine(unsigned long long key, bool active, u64 w, u64 *sum,
+                                             u64 *scratch) {
+  const unsigned act = __ballot_sync(FULL_MASK, active);
+  const int lane = threadIdx.x & 31;
+  bool lead = false;
+  if (active) {
+    const unsigned peers = __match_any_sync(act, key);
+    scratch[lane] = w;
+    __syncwarp(act);
+    if (lane == __ffs(peers) - 1) {
+      u64 s = 0;
+      for (unsigned m = peers; m; m &= m - 1) s += scratch[__ffs(m) - 1];
+      *sum = s;
+      lead = true;
+    }
+  }
+  __syncwarp();
+  return lead;
+}
+
 // Block-wide sum of an i128 (every thread of the block must call); the result
 // is valid in thread 0.  Uses 32 * 16 bytes of the given shared buffer.
 __device__ __forceinline__ i128 block_sum_i128(i128 v, i128 *sbuf) {

@@ -129,6 +129,7 @@ __device__ __forceinline__ int log2_exact(int64_t t) {
 
 template <typename WT>
 __global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine, HubWork hw) {
+  __shared__ u64 wscratch[8][32];
   const int64_t nitems = hw.tot[1];
   for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
     const int64_t k = find_item(hw.ioff, a.list_n, w);
@@ -141,12 +142,21 @@ __global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine,
     int32_t *keys = a.gkeys + hw.toff[k];
     u64 *vals = a.gvals + hw.toff[k];
     const int32_t cbi = refine ? a.CB[i] : 0;
-    for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
-      const int32_t j = a.g.idx[e];
-      if (j == i) continue;
-      if ((uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); continue; }
-      if (refine && a.CB[j] != cbi) continue;
-      hub_table_add(keys, vals, (uint64_t)(t - 1), 32 - lh, a.C[j], (u64)(int64_t)a.g.w[e], &a.ctr[CTR_ERROR]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t cb = c0 + 32 * warp; cb < c1; cb += blockDim.x) {  // warp-uniform chunks
+      const int64_t e = cb + lane;
+      int32_t c = LEIDEN_EMPTY_KEY;
+      u64 wv = 0;
+      if (e < c1) {
+        const int32_t j = a.g.idx[e];
+        bool ok = j != i;
+        if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
+        if (refine && ok && a.CB[j] != cbi) ok = false;
+        if (ok) { c = a.C[j]; wv = (u64)(int64_t)a.g.w[e]; }
+      }
+      u64 sum = 0;
+      if (warp_combine((unsigned long long)(uint32_t)c, c != LEIDEN_EMPTY_KEY, wv, &sum, wscratch[warp]))
+        hub_table_add(keys, vals, (uint64_t)(t - 1), 32 - lh, c, sum, &a.ctr[CTR_ERROR]);
     }
   }
 }

@@ -87,6 +87,22 @@ struct HubWork {
   int64_t *pkid;  //   and the weight towards the hub's own community
 };
 static constexpr int64_t HUB_TABLE_MIN = 4096;
+// Build-time tunables.  LK_AGG_ROUND_SLOTS / LK_HUB_ROUND_SLOTS cap the
+// global hash-table slots (12 B each) processed per round of the aggregation
+// and hub kernels (0: only the scratch capacity limits a round); a cap near
+// 6 Mi keeps a round's tables resident in L2.  LK_AUX_STREAMS is the number of
+// auxiliary streams the tier kernels of a sub-sweep fan out to (0: all on the
+// context stream).
+#ifndef LK_AGG_ROUND_SLOTS
+#define LK_AGG_ROUND_SLOTS 0
+#endif
+#ifndef LK_HUB_ROUND_SLOTS
+#define LK_HUB_ROUND_SLOTS 0
+#endif
+#ifndef LK_AUX_STREAMS
+#define LK_AUX_STREAMS 6
+#endif
+
 
 enum {
   CTR_SCANNED_ENTRIES = 0,

@@ -101,6 +101,8 @@ __global__ void decide_group(MoveArgs<WT> a) {
   u64 *vals = reinterpret_cast<u64 *>(smem) + (size_t)(warp * GPW + gw) * H;
   int32_t *keys = reinterpret_cast<int32_t *>(reinterpret_cast<u64 *>(smem) + (size_t)wpb * GPW * H) +
                   (size_t)(warp * GPW + gw) * H;
+  __shared__ u64 wscratch[8][32];  // blocks of at most 256 threads
+  u64 *wscr = wscratch[warp];
 
   int64_t scanned = 0, nvert = 0, ncand = 0, nmoves = 0;
   i128 accS = 0;
@@ -123,18 +125,33 @@ __global__ void decide_group(MoveArgs<WT> a) {
       for (int s = gl; s < (1 << lh); s += G) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     }
     __syncwarp();
-    if (act) {
-      d = a.C[i];
-      const int32_t cbi = REFINE ? a.CB[i] : 0;
-      for (int64_t e = e0 + gl; e < e1; e += G) {
-        const int32_t j = a.g.idx[e];
-        if (j == i) continue;                           // self = false
-        if ((uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); continue; }
-        if (REFINE && a.CB[j] != cbi) continue;         // scanBounded
-        table_add(keys, vals, lh, a.C[j], (u64)(int64_t)a.g.w[e], &a.ctr[CTR_ERROR]);
-      }
-      if (gl == 0) { scanned += e1 - e0; nvert++; }
+    const int32_t cbi = (REFINE && act) ? a.CB[i] : 0;
+    if (act) d = a.C[i];
+    // warp-uniform walk over the longest row of the warp's groups, so the
+    // lanes can combine equal (group, community) keys before the atomics
+    int64_t span = act ? e1 - e0 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int64_t y = shfl_xor_i64(span, o);
+      span = y > span ? y : span;
     }
+    for (int64_t x0 = 0; x0 < span; x0 += G) {
+      const int64_t e = e0 + x0 + gl;
+      int32_t c = LEIDEN_EMPTY_KEY;
+      u64 wv = 0;
+      if (act && e < e1) {
+        const int32_t j = a.g.idx[e];
+        bool ok = j != i;                               // self = false
+        if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
+        if (REFINE && ok && a.CB[j] != cbi) ok = false;  // scanBounded
+        if (ok) { c = a.C[j]; wv = (u64)(int64_t)a.g.w[e]; }
+      }
+      u64 sum = 0;
+      const unsigned long long key = ((unsigned long long)(uint32_t)gw << 32) | (uint32_t)c;
+      if (warp_combine(key, c != LEIDEN_EMPTY_KEY, wv, &sum, wscr))
+        table_add(keys, vals, lh, c, sum, &a.ctr[CTR_ERROR]);
+    }
+    if (act && gl == 0) { scanned += e1 - e0; nvert++; }
     __syncwarp();
     ST bsc = 0;
     int32_t bc = INT32_MAX;
@@ -221,6 +238,7 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
   __shared__ int32_t r_c[32];
   __shared__ int64_t r_kid[32];
   __shared__ int32_t s_mv;
+  __shared__ u64 wscratch[32][32];
   const int Hmax = 1 << log2H;
   u64 *vals;
   int32_t *keys;
@@ -253,12 +271,22 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
     for (int s = threadIdx.x; s < H; s += blockDim.x) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     __syncthreads();
     const int32_t cbi = REFINE ? a.CB[i] : 0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int32_t j = a.g.idx[e];
-      if (j == i) continue;
-      if ((uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); continue; }
-      if (REFINE && a.CB[j] != cbi) continue;
-      table_add(keys, vals, lh, a.C[j], (u64)(int64_t)a.g.w[e], &a.ctr[CTR_ERROR]);
+    // each warp walks 32-entry chunks (warp-uniform), combining equal
+    // communities across its lanes before the atomics
+    for (int64_t cb = e0 + 32 * warp; cb < e1; cb += 32 * (int64_t)nwarp) {
+      const int64_t e = cb + lane;
+      int32_t c = LEIDEN_EMPTY_KEY;
+      u64 wv = 0;
+      if (e < e1) {
+        const int32_t j = a.g.idx[e];
+        bool ok = j != i;
+        if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
+        if (REFINE && ok && a.CB[j] != cbi) ok = false;
+        if (ok) { c = a.C[j]; wv = (u64)(int64_t)a.g.w[e]; }
+      }
+      u64 sum = 0;
+      if (warp_combine((unsigned long long)(uint32_t)c, c != LEIDEN_EMPTY_KEY, wv, &sum, wscratch[warp]))
+        table_add(keys, vals, lh, c, sum, &a.ctr[CTR_ERROR]);
     }
     if (threadIdx.x == 0) { scanned += e1 - e0; nvert++; }
     __syncthreads();
