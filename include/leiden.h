@@ -180,6 +180,30 @@ int leiden_get_stats(leiden_ctx *ctx, leiden_run_stats *out);
 /* Enables (1) or disables (0) CUDA-event timing of the local-move kernels. */
 int leiden_ctx_set_timing(leiden_ctx *ctx, int32_t enable);
 
+/* Allocation-free modularity.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need a
+ * modularity value -- code under a memory budget that forbids new
+ * allocations, plugins handed a stream but no allocator, or latency-critical
+ * loops that cannot afford the device-wide synchronisation cudaMalloc and
+ * cudaFree imply.  It needs no leiden_ctx and allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  Its scratch (the
+ * per-community totals and accumulators) is one fixed array of about 8 MB in
+ * the library's device image, which every GPU that loads the library holds
+ * until the process exits; graphs above LEIDEN_NOALLOC_MAX_N vertices are
+ * rejected with LEIDEN_ENOMEM.  The first call on a device looks up the
+ * array's device address on that device (make it before any stream capture).
+ * All calls share the array: calls that overlap on the GPU (for example on
+ * two streams) race and must be serialised by the caller.  Computes Eq. 1 at
+ * resolution gamma for membership (DEVICE [n], labels in [0, n)) on g, with
+ * the same integer arithmetic as leiden_modularity; the work is ordered on
+ * cuda_stream (cudaStream_t as void*, NULL = legacy default stream), which the
+ * call synchronises before writing q_out (HOST).  Errors: LEIDEN_EINVAL (bad
+ * gamma, malformed graph, label out of range), LEIDEN_ENOMEM (n too large),
+ * LEIDEN_ECUDA. */
+#define LEIDEN_NOALLOC_MAX_N 1048576
+int leiden_modularity_noalloc(const leiden_csr *g, const int32_t *membership, double gamma,
+                              void *cuda_stream, double *q_out);
+
 /* Detail of the context's last failure (a CUDA error name and message, or a
  * device consistency check), empty if none; owned by the context and valid
  * until its next call. */

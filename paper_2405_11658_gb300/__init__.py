@@ -113,6 +113,8 @@ def lib():
     L.leiden_modularity.restype = C.c_int
     L.leiden_apply_batch.argtypes = [P, P, P, P, P, P, P, i64, P]
     L.leiden_apply_batch.restype = C.c_int
+    L.leiden_modularity_noalloc.argtypes = [P, P, d, P, P]
+    L.leiden_modularity_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -300,12 +302,29 @@ class Context:
         return Graph(off, idx[:nnz.value], w[:nnz.value])
 
 
+NOALLOC_MAX_N = 1048576
+
+
+def modularity_noalloc(g: Graph, memb, gamma: float = 1.0, stream=None) -> float:
+    """Eq. 1 through leiden_modularity_noalloc: no context and no device
+    allocation (for callers that cannot allocate); graphs up to
+    NOALLOC_MAX_N vertices.  Calls that overlap on the GPU share one scratch
+    array and must not run concurrently."""
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    q = C.c_double()
+    gc = g.c()
+    _check(lib().leiden_modularity_noalloc(C.byref(gc), _ptr(memb), gamma, C.c_void_p(st.cuda_stream),
+                                           C.byref(q)), "leiden_modularity_noalloc")
+    return q.value
+
+
 def default_opts() -> dict:
     o = _Opts()
     lib().leiden_opts_default(C.byref(o))
     return {name: getattr(o, name) for name, _ in o._fields_ if name != "reserved"}
 
 
-EXPORTED = ("leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
+EXPORTED = ("leiden_modularity_noalloc", "leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
             "leiden_update", "leiden_modularity", "leiden_apply_batch", "leiden_get_stats",
             "leiden_ctx_set_timing", "leiden_strerror")
