@@ -209,110 +209,247 @@ __global__ void __launch_bounds__(512) agg_block_k(GraphView<WT> g, const int32_
   }
 }
 
-// Global tier, step 1: per listed community, table slots (a power of two >=
-// 2 * min(total degree, |Gamma|) and >= 4096: the community has at most that
-// many distinct neighbour communities), member batches of 256, and 4096-slot
-// drain chunks.
-__global__ void agg_gsize_k(const int32_t *list, int64_t nlist, const int64_t *hoff, const int64_t *coff,
-                            int64_t nc, int64_t *tsz, int64_t *nb, int64_t *nch) {
+// ---------------------------------------------------------------------------
+// Giant communities (total degree above the block tier).  Their entries are
+// partitioned by the hash of the target community into buckets, each sized so
+// that its distinct targets fit a shared-memory table, in three passes over
+// their member rows (count, scatter) plus one over the buckets (hash, emit):
+//   size:    P_k = power of two >= min(tdeg_k, |Gamma|) / BUCKET_KEYS buckets;
+//   count:   entries per bucket (warp-combined atomics);
+//   scan:    bucket offsets in the scratch array;
+//   scatter: (target, weight) pairs into their bucket's range of the scratch;
+//   hash:    one block per bucket builds its table in shared memory, emits the
+//            distinct targets into the community's hole range and resets the
+//            scratch it read.
+// No hash table lives in DRAM, so no atomic has to go there.
+// ---------------------------------------------------------------------------
+static constexpr int BUCKET_KEYS = 2048;      // expected distinct targets per bucket
+static constexpr int64_t AGG_WINDOW = 512;    // flat entries per warp work item
+static constexpr int BUCKET_LOG2H = 13;       // 8192-slot table (96 KB): 4x headroom
+
+__global__ void agg_bsize_k(const int32_t *list, int64_t nlist, const int64_t *hoff, int64_t nc, int64_t *nbk,
+                            int64_t *nwin) {
   GSTRIDE(k, nlist) {
     const int32_t c = list[k];
     const int64_t d = hoff[c + 1] - hoff[c];
     const int64_t cap = d < nc ? d : nc;
-    int64_t h = HUB_TABLE_MIN;
-    while (h < 2 * cap) h <<= 1;
-    tsz[k] = h;
-    nb[k] = (coff[c + 1] - coff[c] + 255) / 256;
-    nch[k] = h / HUB_TABLE_MIN;
+    int64_t P = 1;
+    while (P * BUCKET_KEYS < cap) P <<= 1;
+    nbk[k] = P;
+    nwin[k] = (d + AGG_WINDOW - 1) / AGG_WINDOW;
   }
 }
 
-// Global tier, step 2: every block takes one batch of 256 members of one
-// community (found by binary search over the batch offsets) and adds their
-// rows to the community's table in global scratch.
+// Degree of the member at each position of the community-vertex array, for
+// the prefix sums that place every entry of a community in its flat range.
 template <typename WT>
-__global__ void __launch_bounds__(256) agg_ginsert_k(GraphView<WT> g, const int32_t *C, const int32_t *list,
-                                                     int64_t k0, int64_t k1, const int64_t *boff,
-                                                     const int64_t *tbase, const int64_t *tsz,
-                                                     const int64_t *coff, const int32_t *cv,
-                                                     int32_t *gkeys, u64 *gvals, u64 *err) {
-  __shared__ u64 wscratch[8][32];
-  const int64_t nitems = boff[k1] - boff[k0];
-  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int64_t b = boff[k0] + item;
-    int64_t lo = k0, hi = k1 - 1;  // last k with boff[k] <= b
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (boff[mid] <= b) lo = mid; else hi = mid - 1;
-    }
-    const int64_t k = lo;
-    const int32_t c = list[k];
-    const int64_t mfirst = coff[c] + (b - boff[k]) * 256;
-    int64_t mlast = mfirst + 256;
-    if (mlast > coff[c + 1]) mlast = coff[c + 1];
-    const int64_t H = tsz[k];
-    int lh = 0;
-    while (((int64_t)1 << lh) < H) lh++;
-    int32_t *keys = gkeys + (tbase[k] - tbase[k0]);
-    u64 *vals = gvals + (tbase[k] - tbase[k0]);
-    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    warp_rows_into_table(g, C, cv, mfirst + 32 * warp, mlast, 32 * nwarp, keys, vals,
-                         (uint32_t)(H - 1), 32 - lh, err, wscratch[warp]);
+__global__ void agg_member_deg_k(GraphView<WT> g, const int32_t *cv, int64_t n, int64_t *mdeg) {
+  GSTRIDE(p, n) {
+    const int32_t v = cv[p];
+    mdeg[p] = g.off[v + 1] - g.off[v];
   }
 }
 
-// Global tier, step 3: every block drains one 4096-slot chunk of one table
-// into the community's hole range (positions reserved with atomics on the
-// community's entry count) and resets the slots it read, leaving the scratch
-// empty for its next user.
-__global__ void __launch_bounds__(256) agg_gemit_k(const int32_t *list, int64_t k0, int64_t k1,
-                                                   const int64_t *choff, const int64_t *tbase,
-                                                   const int64_t *hoff, int32_t *gkeys, u64 *gvals,
-                                                   int32_t *hidx, int64_t *hw, int64_t *cdist, int64_t *Kout) {
-  const int64_t nitems = choff[k1] - choff[k0];
+// The warp walks the entries [w0, w1) of one community's flattened rows
+// (members cv[p_lo .. p_hi), pdeg = exclusive prefix of their degrees, so the
+// community's flat range starts at pdeg[p_lo]) and calls f(target, weight,
+// active) warp-uniformly, 32 entries at a time.
+template <typename WT, typename F>
+__device__ __forceinline__ void foreach_window(const GraphView<WT> &g, const int32_t *C, const int32_t *cv,
+                                               const int64_t *pdeg, int64_t p_lo, int64_t p_hi, int64_t w0,
+                                               int64_t w1, u64 *err, F f) {
   const int lane = threadIdx.x & 31;
-  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int64_t b = choff[k0] + item;
-    int64_t lo = k0, hi = k1 - 1;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (choff[mid] <= b) lo = mid; else hi = mid - 1;
+  // first member whose range reaches past w0
+  int64_t lo = p_lo, hi = p_hi - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (pdeg[mid + 1] > w0) hi = mid; else lo = mid + 1;
+  }
+  for (int64_t pb = lo; pb < p_hi; pb += 32) {
+    if (pdeg[pb] >= w1) break;  // same address for every lane: uniform
+    const int64_t m = pb + lane;
+    int64_t rs = 0, cnt = 0;
+    if (m < p_hi) {
+      const int64_t fs0 = pdeg[m], fe0 = pdeg[m + 1];
+      const int64_t fs = fs0 > w0 ? fs0 : w0, fe = fe0 < w1 ? fe0 : w1;
+      if (fe > fs) {
+        rs = g.off[cv[m]] + (fs - fs0);
+        cnt = fe - fs;
+      }
     }
-    const int64_t k = lo;
+    int64_t incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = shfl_i64(incl, (lane - o) & 31);
+      if (lane >= o) incl += y;
+    }
+    const int64_t total = shfl_i64(incl, 31);
+    for (int64_t t0 = 0; t0 < total; t0 += 32) {
+      const int64_t t = t0 + lane;
+      int k = 0;
+#pragma unroll
+      for (int b = 16; b; b >>= 1) {
+        const int64_t v = shfl_i64(incl, k + b - 1);
+        if (v <= t) k += b;
+      }
+      const int64_t sk = shfl_i64(rs, k), ik = shfl_i64(incl, k), dk = shfl_i64(cnt, k);
+      int32_t c = LEIDEN_EMPTY_KEY;
+      u64 wv = 0;
+      if (t < total) {
+        const int64_t e = sk + (t - (ik - dk));
+        const int32_t j = (e >= sk && e < sk + dk) ? g.idx[e] : -1;
+        if ((uint32_t)j < (uint32_t)g.n) { c = C[j]; wv = (u64)(int64_t)g.w[e]; }
+        else atomicOr(err, 64ull);
+      }
+      f(c, wv, c != LEIDEN_EMPTY_KEY);
+    }
+  }
+}
+
+// Work item b belongs to the last k with offs[k] <= b.
+__device__ __forceinline__ int64_t find_k(const int64_t *offs, int64_t n, int64_t b) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (offs[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int64_t bucket_of(int32_t c, int64_t P) {
+  int lp = 0;
+  while (((int64_t)1 << lp) < P) lp++;
+  return lp ? (int64_t)(hash32(c) >> (32 - lp)) : 0;
+}
+
+// PASS = 0: count entries per bucket.  PASS = 1: scatter them.  Work item =
+// one warp-sized window of AGG_WINDOW entries of one giant community.
+template <int PASS, typename WT>
+__global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_t *C, const int32_t *list,
+                                                   int64_t nlist, const int64_t *wnoff, const int64_t *nbk,
+                                                   const int64_t *bkoff, const int64_t *coff, const int64_t *hoff,
+                                                   const int32_t *cv, const int64_t *pdeg, u64 *bcnt,
+                                                   const int64_t *bpos, int32_t *skeys, u64 *svals, u64 *err) {
+  const int64_t nitems = wnoff[nlist];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwg = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = w0g; it < nitems; it += nwg) {  // uniform per warp
+    const int64_t k = find_k(wnoff, nlist, it);
     const int32_t c = list[k];
-    const int64_t s0 = (tbase[k] - tbase[k0]) + (b - choff[k]) * HUB_TABLE_MIN;
+    const int64_t fw0 = hoff[c] + (it - wnoff[k]) * AGG_WINDOW;
+    const int64_t fw1 = fw0 + AGG_WINDOW < hoff[c + 1] ? fw0 + AGG_WINDOW : hoff[c + 1];
+    const int64_t P = nbk[k], base = bkoff[k];
+    foreach_window(g, C, cv, pdeg, coff[c], coff[c + 1], fw0, fw1, err, [&](int32_t d, u64 w, bool act) {
+      const int64_t bk = act ? base + bucket_of(d, P) : -1;
+      // lanes of the same bucket share one atomic
+      const unsigned am = __ballot_sync(FULL_MASK, act);
+      if (act) {
+        const unsigned peers = __match_any_sync(am, (unsigned long long)bk);
+        const int leader = __ffs(peers) - 1;
+        if (PASS == 0) {
+          if (lane == leader) atomicAdd(&bcnt[bk], (u64)__popc(peers));
+        } else {
+          u64 slot0 = 0;
+          if (lane == leader) slot0 = atomicAdd(&bcnt[bk], (u64)__popc(peers));
+          slot0 = __shfl_sync(peers, slot0, leader);
+          const int64_t pos = bpos[bk] + (int64_t)slot0 + __popc(peers & ((1u << lane) - 1u));
+          skeys[pos] = d;
+          svals[pos] = w;
+        }
+      }
+      __syncwarp();
+    });
+  }
+}
+
+// One block per bucket: hash the bucket's pairs in shared memory, emit the
+// distinct targets into the community's hole range, reset the scratch.
+__global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, int64_t nlist, const int64_t *nbk,
+                                                   const int64_t *bkoff, const int64_t *bpos, int32_t *skeys,
+                                                   u64 *svals, const int64_t *hoff, int32_t *hidx, int64_t *hw,
+                                                   int64_t *cdist, int64_t *Kout, u64 *err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int H = 1 << BUCKET_LOG2H;
+  u64 *vals = reinterpret_cast<u64 *>(smem);
+  int32_t *keys = reinterpret_cast<int32_t *>(vals + H);
+  __shared__ u64 wscratch[16][32];
+  __shared__ int64_t s_ws;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int64_t nb = bkoff[nlist];
+  for (int64_t bk = blockIdx.x; bk < nb; bk += gridDim.x) {
+    const int64_t k = find_k(bkoff, nlist, bk);
+    const int32_t c = list[k];
+    int lp = 0;
+    while (((int64_t)1 << lp) < nbk[k]) lp++;
+    const int64_t p0 = bpos[bk], p1 = bpos[bk + 1];
+    for (int x = threadIdx.x; x < H; x += blockDim.x) { keys[x] = LEIDEN_EMPTY_KEY; vals[x] = 0; }
+    if (threadIdx.x == 0) s_ws = 0;
+    __syncthreads();
+    for (int64_t pb = p0 + 32 * warp; pb < p1; pb += 32 * (int64_t)nwarp) {  // warp-uniform
+      const int64_t pos = pb + lane;
+      int32_t d = LEIDEN_EMPTY_KEY;
+      u64 w = 0;
+      if (pos < p1) {
+        d = skeys[pos];
+        w = svals[pos];
+        skeys[pos] = LEIDEN_EMPTY_KEY;  // leave the scratch empty
+        svals[pos] = 0;
+      }
+      u64 sum = 0;
+      if (warp_combine((unsigned long long)(uint32_t)d, d != LEIDEN_EMPTY_KEY, w, &sum, wscratch[warp])) {
+        // the bucket's keys share their top lp hash bits: index by the next ones
+        const uint32_t mask = H - 1;
+        uint32_t sl = (uint32_t)((hash32(d) << lp) >> (32 - BUCKET_LOG2H));
+        bool done = false;
+        for (uint32_t probe = 0; probe < (uint32_t)H && !done; probe++) {
+          const int32_t kk = *(volatile int32_t *)&keys[sl];
+          if (kk == d) { atomicAdd(&vals[sl], sum); done = true; }
+          else if (kk == LEIDEN_EMPTY_KEY) {
+            const int32_t old = atomicCAS(&keys[sl], LEIDEN_EMPTY_KEY, d);
+            if (old == LEIDEN_EMPTY_KEY || old == d) { atomicAdd(&vals[sl], sum); done = true; }
+          }
+          sl = (sl + 1) & mask;
+        }
+        if (!done) atomicOr(err, 16ull);
+      }
+    }
+    __syncthreads();
     int64_t ws = 0;
-    for (int64_t x = threadIdx.x; x < HUB_TABLE_MIN; x += blockDim.x) {  // uniform per warp
-      const int64_t sl = s0 + x;
-      const int32_t key = gkeys[sl];
+    for (int x0 = 32 * warp; x0 < H; x0 += 32 * nwarp) {  // warp-uniform
+      const int x = x0 + lane;
+      const int32_t key = keys[x];
       const bool occ = key != LEIDEN_EMPTY_KEY;
-      const u64 pos = warp_reserve((u64 *)&cdist[c], occ);
+      const u64 slot = warp_reserve((u64 *)&cdist[c], occ);
       if (occ) {
-        const int64_t v = (int64_t)gvals[sl];
-        gkeys[sl] = LEIDEN_EMPTY_KEY;
-        gvals[sl] = 0;
-        hidx[hoff[c] + (int64_t)pos] = key;
-        hw[hoff[c] + (int64_t)pos] = v;
+        const int64_t v = (int64_t)vals[x];
+        hidx[hoff[c] + (int64_t)slot] = key;
+        hw[hoff[c] + (int64_t)slot] = v;
         ws += v;
       }
     }
     for (int o = 16; o; o >>= 1) ws += shfl_xor_i64(ws, o);
-    if (lane == 0 && ws) atomicAdd((u64 *)&Kout[c], (u64)ws);
+    if (lane == 0 && ws) atomicAdd((u64 *)&s_ws, (u64)ws);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ws) atomicAdd((u64 *)&Kout[c], (u64)s_ws);
+    __syncthreads();
   }
 }
 
-// Compaction: each warp takes 32 communities and copies their hole ranges
-// to the compact CSR as one flattened range (prefix sums across the lanes,
-// binary search per entry), so short rows still move in full warps.
-__global__ void agg_compact_k(int64_t nc, const int64_t *hoff, const int64_t *off2, const int32_t *hidx,
-                              const int64_t *hw, int32_t *idx2, int64_t *w2) {
+// ---------------------------------------------------------------------------
+// Compaction of the hole ranges into the final CSR.
+// ---------------------------------------------------------------------------
+// Small communities: each warp takes 32 of them and copies their ranges as
+// one flattened range (prefix sums across the lanes, binary search per entry).
+__global__ void agg_compact_small_k(const int32_t *list, int64_t nlist, const int64_t *hoff, const int64_t *off2,
+                                    const int32_t *hidx, const int64_t *hw, int32_t *idx2, int64_t *w2) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t cb = w0 * 32; cb < nc; cb += nw * 32) {
-    const int64_t c = cb + lane;
+  for (int64_t cb = w0 * 32; cb < nlist; cb += nw * 32) {
+    const int64_t li = cb + lane;
     int64_t src = 0, dst = 0, len = 0;
-    if (c < nc) {
+    if (li < nlist) {
+      const int32_t c = list[li];
       src = hoff[c];
       dst = off2[c];
       len = off2[c + 1] - dst;
@@ -338,6 +475,48 @@ __global__ void agg_compact_k(int64_t nc, const int64_t *hoff, const int64_t *of
         idx2[dk + x] = hidx[sk + x];
         w2[dk + x] = hw[sk + x];
       }
+    }
+  }
+}
+
+// Mid-size communities: one block each.
+__global__ void agg_compact_block_k(const int32_t *list, int64_t nlist, const int64_t *hoff, const int64_t *off2,
+                                    const int32_t *hidx, const int64_t *hw, int32_t *idx2, int64_t *w2) {
+  for (int64_t li = blockIdx.x; li < nlist; li += gridDim.x) {
+    const int32_t c = list[li];
+    const int64_t src = hoff[c], dst = off2[c], len = off2[c + 1] - dst;
+    for (int64_t x = threadIdx.x; x < len; x += blockDim.x) {
+      idx2[dst + x] = hidx[src + x];
+      w2[dst + x] = hw[src + x];
+    }
+  }
+}
+
+// Giant communities: output lengths in windows of AGG_WINDOW entries, one
+// warp per window.
+__global__ void agg_cwin_k(const int32_t *list, int64_t nlist, const int64_t *off2, int64_t *nwin) {
+  GSTRIDE(k, nlist) {
+    const int32_t c = list[k];
+    nwin[k] = (off2[c + 1] - off2[c] + AGG_WINDOW - 1) / AGG_WINDOW;
+  }
+}
+__global__ void agg_compact_win_k(const int32_t *list, int64_t nlist, const int64_t *wnoff, const int64_t *hoff,
+                                  const int64_t *off2, const int32_t *hidx, const int64_t *hw, int32_t *idx2,
+                                  int64_t *w2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwg = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nitems = wnoff[nlist];
+  for (int64_t it = w0g; it < nitems; it += nwg) {
+    const int64_t k = find_k(wnoff, nlist, it);
+    const int32_t c = list[k];
+    const int64_t len = off2[c + 1] - off2[c];
+    const int64_t x0 = (it - wnoff[k]) * AGG_WINDOW;
+    const int64_t x1 = x0 + AGG_WINDOW < len ? x0 + AGG_WINDOW : len;
+    const int64_t src = hoff[c], dst = off2[c];
+    for (int64_t x = x0 + lane; x < x1; x += 32) {
+      idx2[dst + x] = hidx[src + x];
+      w2[dst + x] = hw[src + x];
     }
   }
 }
@@ -403,51 +582,61 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       k<<<(unsigned)blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx, wk.hw,
                                                   wk.cdist, Kout, T.log2H, err);
     } else {
-      // table sizes, member batches and drain chunks of the listed communities
-      int64_t *tsz = wk.off2tmp;                    // [nl]
-      int64_t *tbase = wk.off2tmp + (nl + 1);       // [nl+1]
-      int64_t *nb = wk.off2tmp + 2 * (nl + 1);      // [nl]
-      int64_t *boff = wk.off2tmp + 3 * (nl + 1);    // [nl+1]
-      int64_t *nch = wk.off2tmp + 4 * (nl + 1);     // [nl]
-      int64_t *choff = wk.off2tmp + 5 * (nl + 1);   // [nl+1]
-      agg_gsize_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, wk.hoff, wk.coff, nc, tsz, nb, nch);
-      exclusive_scan<int64_t>(tsz, tbase, nl, wk.scan_tmp, s);
-      exclusive_scan<int64_t>(nb, boff, nl, wk.scan_tmp, s);
-      exclusive_scan<int64_t>(nch, choff, nl, wk.scan_tmp, s);
-      // Rounds: the tables of one round fit in a slot budget sized to stay
-      // resident in L2, so the insert atomics do not go to DRAM (a single
-      // table larger than the budget gets a round of its own).
-      cudaMemcpyAsync(&wk.h_koff[MAX_TIERS + 1], tbase + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+      // giant communities: buckets sized for a shared-memory table
+      int64_t *nbk = wk.off2tmp;                    // [nl]   buckets per community
+      int64_t *bkoff = wk.off2tmp + (nl + 1);       // [nl+1] bucket index offsets
+      int64_t *nwin = wk.off2tmp + 2 * (nl + 1);    // [nl]   entry windows
+      int64_t *wnoff = wk.off2tmp + 3 * (nl + 1);   // [nl+1]
+      agg_bsize_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, wk.hoff, nc, nbk, nwin);
+      exclusive_scan<int64_t>(nbk, bkoff, nl, wk.scan_tmp, s);
+      exclusive_scan<int64_t>(nwin, wnoff, nl, wk.scan_tmp, s);
+      // member-degree prefix over the community-vertex array: pdeg[coff[c]] =
+      // hoff[c], so every community's entries form one flat range
+      int64_t *mdeg = wk.ccur;      // free after the placement
+      int64_t *pdeg = wk.scanned;   // free after the tier lists were read
+      agg_member_deg_k<WT><<<gridn(n, 256), 256, 0, s>>>(g, wk.cv, n, mdeg);
+      exclusive_scan<int64_t>(mdeg, pdeg, n, wk.scan_tmp, s);
+      cudaMemcpyAsync(&wk.h_koff[MAX_TIERS + 1], bkoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) return LEIDEN_ECUDA;
-      const int64_t total_slots = wk.h_koff[MAX_TIERS + 1];
-      const int64_t budget = (LK_AGG_ROUND_SLOTS > 0 && LK_AGG_ROUND_SLOTS < wk.gcap) ? LK_AGG_ROUND_SLOTS : wk.gcap;
-      std::vector<int64_t> h_tb;
-      if (total_slots > budget) {
-        h_tb.resize(nl + 1);
-        if (cudaMemcpy(h_tb.data(), tbase, (nl + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
-          return LEIDEN_ECUDA;
-      }
-      int64_t k0 = 0;
-      while (k0 < nl) {
-        int64_t k1 = nl;
-        if (total_slots > budget) {
-          k1 = k0 + 1;
-          while (k1 < nl && h_tb[k1 + 1] - h_tb[k0] <= budget) k1++;
-          if (h_tb[k1] - h_tb[k0] > wk.gcap) return LEIDEN_ENOMEM;
-        }
-        // scratch tables are empty on entry (every user drains and resets them)
-        agg_ginsert_k<WT><<<(unsigned)(wk.sms * 8), 256, 0, s>>>(g, C, list, k0, k1, boff, tbase, tsz, wk.coff,
-                                                                 wk.cv, wk.gkeys, wk.gvals, err);
-        agg_gemit_k<<<(unsigned)(wk.sms * 8), 256, 0, s>>>(list, k0, k1, choff, tbase, wk.hoff, wk.gkeys, wk.gvals,
-                                                            wk.hidx, wk.hw, wk.cdist, Kout);
-        k0 = k1;
-      }
+      const int64_t nb = wk.h_koff[MAX_TIERS + 1];
+      if (nb + 1 > wk.bcap) return LEIDEN_ENOMEM;
+      cudaMemsetAsync(wk.bcnt, 0, (size_t)(nb + 1) * sizeof(u64), s);
+      const unsigned grid = (unsigned)(wk.sms * 16);
+      agg_bpass_k<0, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
+                                               wk.bcnt, nullptr, nullptr, nullptr, err);
+      exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(wk.bcnt), wk.bpos, nb, wk.scan_tmp, s);
+      cudaMemsetAsync(wk.bcnt, 0, (size_t)(nb + 1) * sizeof(u64), s);
+      // the bucket ranges tile [0, sum of the listed total degrees) of the
+      // scratch arrays, which are empty on entry and left empty
+      agg_bpass_k<1, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
+                                               wk.bcnt, wk.bpos, wk.gkeys, wk.gvals, err);
+      const size_t smem = (size_t)(1u << BUCKET_LOG2H) * 12;
+      ensure_smem((const void *)agg_bhash_k, smem);
+      agg_bhash_k<<<(unsigned)(wk.sms * 2), 512, smem, s>>>(list, nl, nbk, bkoff, wk.bpos, wk.gkeys, wk.gvals,
+                                                            wk.hoff, wk.hidx, wk.hw, wk.cdist, Kout, err);
     }
   }
   exclusive_scan<int64_t>(wk.cdist, off2, nc, wk.scan_tmp, s);
   cudaMemcpyAsync(nnz2, off2 + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-  agg_compact_k<<<gridn(nc * 32, 256, (int64_t)wk.sms * 32), 256, 0, s>>>(nc, wk.hoff, off2, wk.hidx, wk.hw,
-                                                                        idx2, w2);
+  for (int t = 1; t < tt.ntiers; t++) {
+    const int32_t *list = wk.clist + koff[t];
+    const int64_t nl = koff[t + 1] - koff[t];
+    if (nl <= 0) continue;
+    if (tt.t[t].kind == TIER_GROUP)
+      agg_compact_small_k<<<gridn(nl, 256, (int64_t)wk.sms * 32), 256, 0, s>>>(list, nl, wk.hoff, off2, wk.hidx,
+                                                                              wk.hw, idx2, w2);
+    else if (tt.t[t].kind == TIER_BLOCK)
+      agg_compact_block_k<<<(unsigned)(nl < wk.sms * 8 ? nl : wk.sms * 8), 256, 0, s>>>(list, nl, wk.hoff, off2,
+                                                                                      wk.hidx, wk.hw, idx2, w2);
+    else {
+      int64_t *nwin = wk.off2tmp;
+      int64_t *wnoff = wk.off2tmp + (nl + 1);
+      agg_cwin_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, off2, nwin);
+      exclusive_scan<int64_t>(nwin, wnoff, nl, wk.scan_tmp, s);
+      agg_compact_win_k<<<(unsigned)(wk.sms * 16), 256, 0, s>>>(list, nl, wnoff, wk.hoff, off2, wk.hidx, wk.hw,
+                                                                 idx2, w2);
+    }
+  }
   return 0;
 }
 

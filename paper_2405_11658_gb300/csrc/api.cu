@@ -44,6 +44,9 @@ struct leiden_ctx {
   u64 *gvals;
   int64_t gcap = 0;
   int32_t *big;
+  u64 *bcnt;
+  int64_t *bpos;
+  int64_t bcap = 0;
   HubWork hub{};
   int64_t hub_items = 0;
   u64 *ctr;
@@ -409,6 +412,7 @@ AggWork agg_work(leiden_ctx *c) {
   w.hidx = c->hidx; w.hw = c->hw; w.gkeys = c->gkeys; w.gvals = c->gvals; w.gcap = c->gcap;
   w.blockhist = c->blockhist; w.scanned = c->scanned; w.koff_dev = c->koff_dev; w.scan_tmp = c->scan_tmp;
   w.h_koff = c->h_koff; w.Kout = c->Kp; w.ctr = c->ctr; w.sms = c->sms;
+  w.bcnt = c->bcnt; w.bpos = c->bpos; w.bcap = c->bcap;
   return w;
 }
 
@@ -682,6 +686,10 @@ int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_
   rc |= dal(c, &c->gkeys, c->gcap); rc |= dal(c, &c->gvals, c->gcap);
   rc |= dal(c, &c->ctr, CTR_COUNT);
   rc |= dal(c, &c->big, n1);
+  // giant-community buckets: a community of total degree T > 2048 gets at most
+  // 2 * ceil(T / 2048) <= T / 512 buckets, so the total stays below nnz / 512
+  c->bcap = m / 256 + n1 + 16;
+  rc |= dal(c, &c->bcnt, c->bcap); rc |= dal(c, &c->bpos, c->bcap);
   rc |= dal(c, &c->hub.tsz, n1); rc |= dal(c, &c->hub.toff, n1);
   rc |= dal(c, &c->hub.ioff, n1); rc |= dal(c, &c->hub.soff, n1);
   rc |= dal(c, &c->hub.tot, 4);

@@ -205,6 +205,9 @@ struct AggWork {
   int64_t *scan_tmp;
   int64_t *h_koff;       // pinned host, >= MAX_TIERS + 3 entries
   int64_t *Kout;         // [nc] row sums of the super-vertex graph (its K')
+  u64 *bcnt;             // [bcap] giant-community bucket counters
+  int64_t *bpos;         // [bcap] bucket offsets in the scratch arrays
+  int64_t bcap;
   u64 *ctr;
   int sms;
 };
