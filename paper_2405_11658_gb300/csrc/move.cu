@@ -43,6 +43,40 @@ __device__ __forceinline__ void table_add(int32_t *keys, u64 *vals, int log2H, i
   atomicOr(err, 16ull);
 }
 
+// Scans table slots s0, s0 + step, ... < H of one vertex: candidate scores
+// for every occupied slot other than the own community d, and the weight to
+// d.  SCAN_UNROLL slots per lane are loaded first and their Sigma'[c] gathers
+// issued together, so the gathers overlap instead of running back to back.
+static constexpr int SCAN_UNROLL = LK_SCAN_UNROLL;
+static constexpr int ROW_UNROLL = LK_ROW_UNROLL;  // row entries per lane in flight in the decide kernels
+template <typename ST>
+__device__ __forceinline__ void scan_slots(const int32_t *keys, const u64 *vals, int H, int s0, int step,
+                                           int32_t d, ST A, ST B, const int64_t *Sig, ST &bsc, int32_t &bc,
+                                           int64_t &kid, int64_t &ncand) {
+  for (int sb = s0; sb < H; sb += step * SCAN_UNROLL) {
+    int32_t ck[SCAN_UNROLL];
+    int64_t vk[SCAN_UNROLL], sg[SCAN_UNROLL];
+#pragma unroll
+    for (int u = 0; u < SCAN_UNROLL; u++) {
+      const int sl = sb + u * step;
+      ck[u] = sl < H ? keys[sl] : LEIDEN_EMPTY_KEY;
+      vk[u] = ck[u] != LEIDEN_EMPTY_KEY ? (int64_t)vals[sl] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < SCAN_UNROLL; u++)
+      sg[u] = (ck[u] != LEIDEN_EMPTY_KEY && ck[u] != d) ? Sig[ck[u]] : 0;
+#pragma unroll
+    for (int u = 0; u < SCAN_UNROLL; u++) {
+      const int32_t c = ck[u];
+      if (c == LEIDEN_EMPTY_KEY) continue;
+      ncand++;
+      if (c == d) { kid = vk[u]; continue; }
+      const ST sc = A * (ST)vk[u] - B * (ST)sg[u];
+      if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
+    }
+  }
+}
+
 // Eligibility of vertex i, decided by one thread.
 template <bool REFINE, typename WT>
 __device__ __forceinline__ bool eligible(const MoveArgs<WT> &a, int32_t i) {
@@ -135,21 +169,35 @@ __global__ void decide_group(MoveArgs<WT> a) {
       const int64_t y = shfl_xor_i64(span, o);
       span = y > span ? y : span;
     }
-    for (int64_t x0 = 0; x0 < span; x0 += G) {
-      const int64_t e = e0 + x0 + gl;
-      int32_t c = LEIDEN_EMPTY_KEY;
-      u64 wv = 0;
-      if (act && e < e1) {
-        const int32_t j = a.g.idx[e];
-        bool ok = j != i;                               // self = false
+    for (int64_t xb = 0; xb < span; xb += (int64_t)G * ROW_UNROLL) {
+      // ROW_UNROLL entries per lane: all loads and gathers first, then the
+      // warp-uniform combine and table updates
+      int32_t cc[ROW_UNROLL];
+      u64 wv[ROW_UNROLL];
+#pragma unroll
+      for (int u = 0; u < ROW_UNROLL; u++) {
+        const int64_t e = e0 + xb + (int64_t)u * G + gl;
+        const bool in = act && e < e1;
+        const int32_t j = in ? a.g.idx[e] : -1;
+        wv[u] = in ? (u64)(int64_t)a.g.w[e] : 0;
+        bool ok = in && j != i;                         // self = false
         if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
-        if (REFINE && ok && a.CB[j] != cbi) ok = false;  // scanBounded
-        if (ok) { c = a.C[j]; wv = (u64)(int64_t)a.g.w[e]; }
+        cc[u] = ok ? j : -1;
       }
-      u64 sum = 0;
-      const unsigned long long key = ((unsigned long long)(uint32_t)gw << 32) | (uint32_t)c;
-      if (warp_combine(key, c != LEIDEN_EMPTY_KEY, wv, &sum, wscr))
-        table_add(keys, vals, lh, c, sum, &a.ctr[CTR_ERROR]);
+#pragma unroll
+      for (int u = 0; u < ROW_UNROLL; u++) {
+        const int32_t j = cc[u];
+        bool ok = j >= 0;
+        if (REFINE && ok && a.CB[j] != cbi) ok = false;  // scanBounded
+        cc[u] = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
+      }
+#pragma unroll
+      for (int u = 0; u < ROW_UNROLL; u++) {
+        u64 sum = 0;
+        const unsigned long long key = ((unsigned long long)(uint32_t)gw << 32) | (uint32_t)cc[u];
+        if (warp_combine(key, cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum, wscr))
+          table_add(keys, vals, lh, cc[u], sum, &a.ctr[CTR_ERROR]);
+      }
     }
     if (act && gl == 0) { scanned += e1 - e0; nvert++; }
     __syncwarp();
@@ -159,15 +207,7 @@ __global__ void decide_group(MoveArgs<WT> a) {
     if (act) {
       const ST A = (ST)a.A;
       const ST B = (ST)a.p * (ST)a.K[i];
-      for (int s = gl; s < (1 << lh); s += G) {
-        const int32_t c = keys[s];
-        if (c == LEIDEN_EMPTY_KEY) continue;
-        ncand++;
-        const int64_t v = (int64_t)vals[s];
-        if (c == d) { kid = v; continue; }
-        const ST sc = A * (ST)v - B * (ST)a.Sig[c];
-        if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
-      }
+      scan_slots<ST>(keys, vals, 1 << lh, gl, G, d, A, B, a.Sig, bsc, bc, kid, ncand);
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
@@ -273,20 +313,33 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
     const int32_t cbi = REFINE ? a.CB[i] : 0;
     // each warp walks 32-entry chunks (warp-uniform), combining equal
     // communities across its lanes before the atomics
-    for (int64_t cb = e0 + 32 * warp; cb < e1; cb += 32 * (int64_t)nwarp) {
-      const int64_t e = cb + lane;
-      int32_t c = LEIDEN_EMPTY_KEY;
-      u64 wv = 0;
-      if (e < e1) {
-        const int32_t j = a.g.idx[e];
-        bool ok = j != i;
+    for (int64_t cb = e0 + 32 * warp; cb < e1; cb += 32 * (int64_t)nwarp * ROW_UNROLL) {
+      int32_t cc[ROW_UNROLL];
+      u64 wv[ROW_UNROLL];
+#pragma unroll
+      for (int u = 0; u < ROW_UNROLL; u++) {
+        const int64_t e = cb + (int64_t)u * 32 * nwarp + lane;
+        const bool in = e < e1;
+        const int32_t j = in ? a.g.idx[e] : -1;
+        wv[u] = in ? (u64)(int64_t)a.g.w[e] : 0;
+        bool ok = in && j != i;
         if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
-        if (REFINE && ok && a.CB[j] != cbi) ok = false;
-        if (ok) { c = a.C[j]; wv = (u64)(int64_t)a.g.w[e]; }
+        cc[u] = ok ? j : -1;
       }
-      u64 sum = 0;
-      if (warp_combine((unsigned long long)(uint32_t)c, c != LEIDEN_EMPTY_KEY, wv, &sum, wscratch[warp]))
-        table_add(keys, vals, lh, c, sum, &a.ctr[CTR_ERROR]);
+#pragma unroll
+      for (int u = 0; u < ROW_UNROLL; u++) {
+        const int32_t j = cc[u];
+        bool ok = j >= 0;
+        if (REFINE && ok && a.CB[j] != cbi) ok = false;
+        cc[u] = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
+      }
+#pragma unroll
+      for (int u = 0; u < ROW_UNROLL; u++) {
+        u64 sum = 0;
+        if (warp_combine((unsigned long long)(uint32_t)cc[u], cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum,
+                         wscratch[warp]))
+          table_add(keys, vals, lh, cc[u], sum, &a.ctr[CTR_ERROR]);
+      }
     }
     if (threadIdx.x == 0) { scanned += e1 - e0; nvert++; }
     __syncthreads();
@@ -295,15 +348,7 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
     ST bsc = 0;
     int32_t bc = INT32_MAX;
     int64_t kid = 0;
-    for (int s = threadIdx.x; s < H; s += blockDim.x) {
-      const int32_t c = keys[s];
-      if (c == LEIDEN_EMPTY_KEY) continue;
-      ncand++;
-      const int64_t v = (int64_t)vals[s];
-      if (c == d) { kid = v; continue; }
-      const ST sc = A * (ST)v - B * (ST)a.Sig[c];
-      if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
-    }
+    scan_slots<ST>(keys, vals, H, threadIdx.x, blockDim.x, d, A, B, a.Sig, bsc, bc, kid, ncand);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const ST osc = shfl_xor_any<ST>(bsc, o);
