@@ -232,6 +232,7 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with Clocks(torch.cuda.current_device()) as clk:
+        launches0 = L.kernel_launches()
         t0 = time.perf_counter()
         e_start = torch.cuda.Event(enable_timing=True)
         e_end = torch.cuda.Event(enable_timing=True)
@@ -241,6 +242,7 @@ def run_ours(args):
         e_end.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        launches = L.kernel_launches() - launches0
     total_ms = e_start.elapsed_time(e_end)
     static_ms = sum(r["static_ms"] for r in rec)
     static_edges = sum(r["static_edges"] for r in rec)
@@ -249,10 +251,10 @@ def run_ours(args):
         import torch.distributed as dist
         t = torch.tensor([total_ms, static_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([static_edges], device=dev, dtype=torch.float64)
+        e = torch.tensor([static_edges, launches], device=dev, dtype=torch.float64)
         dist.all_reduce(e)
         total_ms, static_ms = float(t[0]), float(t[1])
-        static_edges_all = float(e[0])
+        static_edges_all, launches = float(e[0]), int(e[1])  # launches: all ranks
     else:
         static_edges_all = static_edges
     value = static_edges_all / (static_ms / 1000.0)
@@ -333,7 +335,7 @@ def run_ours(args):
                          "ms_per_launch": mv_ms / max(1, mv_launches), "launches": mv_launches},
             "cpu_baseline": base,
             "e2e": e2e,
-            "gpu_launches": None,
+            "gpu_launches": launches,
             "clocks": clk.summary(),
             "wall_s": wall,
         }

@@ -204,6 +204,12 @@ int leiden_ctx_set_timing(leiden_ctx *ctx, int32_t enable);
 int leiden_modularity_noalloc(const leiden_csr *g, const int32_t *membership, double gamma,
                               void *cuda_stream, double *q_out);
 
+/* Number of CUDA kernels this library has enqueued in this process so far,
+ * over all contexts, devices and threads (a relaxed atomic counter; kernels
+ * replayed from a captured CUDA graph count once, at capture).  Callers
+ * difference two readings to count the launches of a region. */
+uint64_t leiden_kernel_launches(void);
+
 /* Detail of the context's last failure (a CUDA error name and message, or a
  * device consistency check), empty if none; owned by the context and valid
  * until its next call. */

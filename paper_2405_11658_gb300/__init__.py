@@ -115,6 +115,8 @@ def lib():
     L.leiden_apply_batch.restype = C.c_int
     L.leiden_modularity_noalloc.argtypes = [P, P, d, P, P]
     L.leiden_modularity_noalloc.restype = C.c_int
+    L.leiden_kernel_launches.argtypes = []
+    L.leiden_kernel_launches.restype = C.c_uint64
     _lib = L
     return L
 
@@ -319,6 +321,12 @@ def modularity_noalloc(g: Graph, memb, gamma: float = 1.0, stream=None) -> float
     return q.value
 
 
+def kernel_launches() -> int:
+    """Kernels the library has enqueued in this process so far
+    (leiden_kernel_launches); difference two readings to count a region."""
+    return int(lib().leiden_kernel_launches())
+
+
 def default_opts() -> dict:
     o = _Opts()
     lib().leiden_opts_default(C.byref(o))
@@ -327,4 +335,4 @@ def default_opts() -> dict:
 
 EXPORTED = ("leiden_modularity_noalloc", "leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
             "leiden_update", "leiden_modularity", "leiden_apply_batch", "leiden_get_stats",
-            "leiden_ctx_set_timing", "leiden_strerror")
+            "leiden_ctx_set_timing", "leiden_strerror", "leiden_kernel_launches")

@@ -541,10 +541,10 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
   cudaMemsetAsync(wk.ctdeg, 0, (size_t)(nc + 1) * sizeof(int64_t), s);
   cudaMemsetAsync(wk.ccur, 0, (size_t)(nc + 1) * sizeof(int64_t), s);
   cudaMemsetAsync(wk.cdist, 0, (size_t)(nc + 1) * sizeof(int64_t), s);
-  if (n > 0) agg_count_k<<<gridn(n, 256), 256, 0, s>>>(n, g.off, C, wk.ccount, wk.ctdeg);
+  if (n > 0) LK_COUNTED agg_count_k<<<gridn(n, 256), 256, 0, s>>>(n, g.off, C, wk.ccount, wk.ctdeg);
   exclusive_scan<int64_t>(wk.ccount, wk.coff, nc, wk.scan_tmp, s);
   exclusive_scan<int64_t>(wk.ctdeg, wk.hoff, nc, wk.scan_tmp, s);
-  if (n > 0) agg_place_k<<<gridn(n, 256), 256, 0, s>>>(n, C, wk.coff, wk.ccur, wk.cv);
+  if (n > 0) LK_COUNTED agg_place_k<<<gridn(n, 256), 256, 0, s>>>(n, C, wk.coff, wk.ccur, wk.cv);
 
   const TierTable tt = agg_tiers();
   launch_buckets(wk.hoff, nc, 0, tt, wk.clist, wk.blockhist, wk.scanned, wk.koff_dev, wk.scan_tmp, s);
@@ -566,12 +566,12 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       const size_t smem = (size_t)(T.threads / 32) * (1u << T.log2H) * 12;
       const unsigned blocks = gridn(nl * 32, T.threads, (int64_t)wk.sms * 16);
       if (T.log2H == 7) {
-        agg_warp_k<7, WT><<<blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx,
+        LK_COUNTED agg_warp_k<7, WT><<<blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx,
                                                           wk.hw, wk.cdist, Kout, err);
       } else {
         auto k = agg_warp_k<10, WT>;
         ensure_smem((const void *)k, smem);
-        k<<<blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx, wk.hw,
+        LK_COUNTED k<<<blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx, wk.hw,
                                           wk.cdist, Kout, err);
       }
     } else if (T.kind == TIER_BLOCK) {
@@ -579,7 +579,7 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       auto k = agg_block_k<WT>;
       ensure_smem((const void *)k, smem);
       int64_t blocks = nl < (int64_t)wk.sms * 4 ? nl : (int64_t)wk.sms * 4;
-      k<<<(unsigned)blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx, wk.hw,
+      LK_COUNTED k<<<(unsigned)blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx, wk.hw,
                                                   wk.cdist, Kout, T.log2H, err);
     } else {
       // giant communities: buckets sized for a shared-memory table
@@ -587,14 +587,14 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       int64_t *bkoff = wk.off2tmp + (nl + 1);       // [nl+1] bucket index offsets
       int64_t *nwin = wk.off2tmp + 2 * (nl + 1);    // [nl]   entry windows
       int64_t *wnoff = wk.off2tmp + 3 * (nl + 1);   // [nl+1]
-      agg_bsize_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, wk.hoff, nc, nbk, nwin);
+      LK_COUNTED agg_bsize_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, wk.hoff, nc, nbk, nwin);
       exclusive_scan<int64_t>(nbk, bkoff, nl, wk.scan_tmp, s);
       exclusive_scan<int64_t>(nwin, wnoff, nl, wk.scan_tmp, s);
       // member-degree prefix over the community-vertex array: pdeg[coff[c]] =
       // hoff[c], so every community's entries form one flat range
       int64_t *mdeg = wk.ccur;      // free after the placement
       int64_t *pdeg = wk.scanned;   // free after the tier lists were read
-      agg_member_deg_k<WT><<<gridn(n, 256), 256, 0, s>>>(g, wk.cv, n, mdeg);
+      LK_COUNTED agg_member_deg_k<WT><<<gridn(n, 256), 256, 0, s>>>(g, wk.cv, n, mdeg);
       exclusive_scan<int64_t>(mdeg, pdeg, n, wk.scan_tmp, s);
       cudaMemcpyAsync(&wk.h_koff[MAX_TIERS + 1], bkoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) return LEIDEN_ECUDA;
@@ -602,17 +602,17 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       if (nb + 1 > wk.bcap) return LEIDEN_ENOMEM;
       cudaMemsetAsync(wk.bcnt, 0, (size_t)(nb + 1) * sizeof(u64), s);
       const unsigned grid = (unsigned)(wk.sms * 16);
-      agg_bpass_k<0, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
+      LK_COUNTED agg_bpass_k<0, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
                                                wk.bcnt, nullptr, nullptr, nullptr, err);
       exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(wk.bcnt), wk.bpos, nb, wk.scan_tmp, s);
       cudaMemsetAsync(wk.bcnt, 0, (size_t)(nb + 1) * sizeof(u64), s);
       // the bucket ranges tile [0, sum of the listed total degrees) of the
       // scratch arrays, which are empty on entry and left empty
-      agg_bpass_k<1, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
+      LK_COUNTED agg_bpass_k<1, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
                                                wk.bcnt, wk.bpos, wk.gkeys, wk.gvals, err);
       const size_t smem = (size_t)(1u << BUCKET_LOG2H) * 12;
       ensure_smem((const void *)agg_bhash_k, smem);
-      agg_bhash_k<<<(unsigned)(wk.sms * 2), 512, smem, s>>>(list, nl, nbk, bkoff, wk.bpos, wk.gkeys, wk.gvals,
+      LK_COUNTED agg_bhash_k<<<(unsigned)(wk.sms * 2), 512, smem, s>>>(list, nl, nbk, bkoff, wk.bpos, wk.gkeys, wk.gvals,
                                                             wk.hoff, wk.hidx, wk.hw, wk.cdist, Kout, err);
     }
   }
@@ -623,17 +623,17 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
     const int64_t nl = koff[t + 1] - koff[t];
     if (nl <= 0) continue;
     if (tt.t[t].kind == TIER_GROUP)
-      agg_compact_small_k<<<gridn(nl, 256, (int64_t)wk.sms * 32), 256, 0, s>>>(list, nl, wk.hoff, off2, wk.hidx,
+      LK_COUNTED agg_compact_small_k<<<gridn(nl, 256, (int64_t)wk.sms * 32), 256, 0, s>>>(list, nl, wk.hoff, off2, wk.hidx,
                                                                               wk.hw, idx2, w2);
     else if (tt.t[t].kind == TIER_BLOCK)
-      agg_compact_block_k<<<(unsigned)(nl < wk.sms * 8 ? nl : wk.sms * 8), 256, 0, s>>>(list, nl, wk.hoff, off2,
+      LK_COUNTED agg_compact_block_k<<<(unsigned)(nl < wk.sms * 8 ? nl : wk.sms * 8), 256, 0, s>>>(list, nl, wk.hoff, off2,
                                                                                       wk.hidx, wk.hw, idx2, w2);
     else {
       int64_t *nwin = wk.off2tmp;
       int64_t *wnoff = wk.off2tmp + (nl + 1);
-      agg_cwin_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, off2, nwin);
+      LK_COUNTED agg_cwin_k<<<gridn(nl, 256), 256, 0, s>>>(list, nl, off2, nwin);
       exclusive_scan<int64_t>(nwin, wnoff, nl, wk.scan_tmp, s);
-      agg_compact_win_k<<<(unsigned)(wk.sms * 16), 256, 0, s>>>(list, nl, wnoff, wk.hoff, off2, wk.hidx, wk.hw,
+      LK_COUNTED agg_compact_win_k<<<(unsigned)(wk.sms * 16), 256, 0, s>>>(list, nl, wnoff, wk.hoff, off2, wk.hidx, wk.hw,
                                                                  idx2, w2);
     }
   }

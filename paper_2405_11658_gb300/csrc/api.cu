@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <vector>
 
@@ -17,6 +18,11 @@
 #include "leiden.h"
 
 using namespace lk;
+
+namespace lk {
+static std::atomic<uint64_t> g_kernel_launches{0};
+void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace lk
 
 struct leiden_ctx {
   cudaStream_t st = nullptr;
@@ -239,7 +245,7 @@ __global__ void count_u8_k(const uint8_t *a, int64_t n, u64 *out) {
 
 int64_t count_flags(leiden_ctx *c, const uint8_t *a, int64_t n) {
   cudaMemsetAsync(&c->ctr[CTR_SCRATCH0], 0, sizeof(u64), c->st);
-  if (n > 0) count_u8_k<<<c->sms * 4, 256, 0, c->st>>>(a, n, &c->ctr[CTR_SCRATCH0]);
+  if (n > 0) LK_COUNTED count_u8_k<<<c->sms * 4, 256, 0, c->st>>>(a, n, &c->ctr[CTR_SCRATCH0]);
   cudaMemcpyAsync(&c->h_ctr[CTR_SCRATCH0], &c->ctr[CTR_SCRATCH0], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
   if (sync(c)) return -1;
   return (int64_t)c->h_ctr[CTR_SCRATCH0];
@@ -250,7 +256,7 @@ int build_buckets(const Run &r, const int64_t *off, int64_t n, Buckets &b) {
   b.nkeys = (1 << r.log2S) * c->tiers.ntiers;
   launch_buckets(off, n, r.log2S, c->tiers, c->vlist, c->blockhist, c->scanned, c->koff_dev, c->scan_tmp, c->st);
   cudaMemsetAsync(&c->ctr[CTR_SCRATCH0], 0, sizeof(u64), c->st);
-  if (n > 0) maxdeg_k<<<c->sms * 4, 256, 0, c->st>>>(off, n, &c->ctr[CTR_SCRATCH0]);
+  if (n > 0) LK_COUNTED maxdeg_k<<<c->sms * 4, 256, 0, c->st>>>(off, n, &c->ctr[CTR_SCRATCH0]);
   cudaMemcpyAsync(c->h_koff, c->koff_dev, (size_t)(b.nkeys + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c->st);
   cudaMemcpyAsync(&c->h_ctr[CTR_SCRATCH0], &c->ctr[CTR_SCRATCH0], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
   int rc = sync(c);
@@ -638,6 +644,8 @@ void leiden_opts_default(leiden_opts *o) {
   o->det_subsets = 8;
   o->refine_all_first_pass = 0;
 }
+
+uint64_t leiden_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 const char *leiden_strerror(int code) {
   switch (code) {

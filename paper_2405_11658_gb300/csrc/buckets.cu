@@ -72,12 +72,12 @@ void launch_buckets(const int64_t *off, int64_t n, int log2S, const TierTable &t
   const int nkeys = (1 << log2S) * tt.ntiers;
   int64_t nb = (n + BK_CHUNK - 1) / BK_CHUNK;
   if (nb < 1) nb = 1;
-  bucket_count_k<<<(unsigned)nb, BK_THREADS, nkeys * sizeof(int32_t), s>>>(off, n, log2S, tm, nkeys,
+  LK_COUNTED bucket_count_k<<<(unsigned)nb, BK_THREADS, nkeys * sizeof(int32_t), s>>>(off, n, log2S, tm, nkeys,
                                                                           blockhist);
   exclusive_scan<int32_t>(blockhist, scanned, nb * nkeys, scan_tmp, s);
-  bucket_scatter_k<<<(unsigned)nb, BK_THREADS, nkeys * sizeof(int64_t), s>>>(off, n, log2S, tm, nkeys,
+  LK_COUNTED bucket_scatter_k<<<(unsigned)nb, BK_THREADS, nkeys * sizeof(int64_t), s>>>(off, n, log2S, tm, nkeys,
                                                                             scanned, list);
-  bucket_koff_k<<<1, 256, 0, s>>>(scanned, nkeys, nb, koff_dev);
+  LK_COUNTED bucket_koff_k<<<1, 256, 0, s>>>(scanned, nkeys, nb, koff_dev);
 }
 
 }  // namespace lk

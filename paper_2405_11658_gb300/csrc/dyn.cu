@@ -113,17 +113,17 @@ void launch_mark_ds(int64_t n, const int64_t *off, const int32_t *idx, const int
   if (n <= 0) return;
   cudaMemsetAsync(wk.dE, 0, (size_t)n, s);
   cudaMemsetAsync(wk.dC, 0, (size_t)n, s);
-  if (nd > 0) ds_del_k<<<gridd(nd, 256), 256, 0, s>>>(nd, ds, dd, Cprev, affected, wk.dE, wk.dC);
+  if (nd > 0) LK_COUNTED ds_del_k<<<gridd(nd, 256), 256, 0, s>>>(nd, ds, dd, Cprev, affected, wk.dE, wk.dC);
   if (ni > 0) {
     cudaMemsetAsync(wk.cnt, 0, (size_t)(n + 1) * sizeof(int64_t), s);
     cudaMemsetAsync(wk.cur, 0, (size_t)(n + 1) * sizeof(int64_t), s);
-    ds_cnt_k<<<gridd(ni, 256), 256, 0, s>>>(ni, is, id, wk.cnt);
+    LK_COUNTED ds_cnt_k<<<gridd(ni, 256), 256, 0, s>>>(ni, is, id, wk.cnt);
     exclusive_scan<int64_t>(wk.cnt, wk.soff, n, wk.scan_tmp, s);
-    ds_place_k<<<gridd(ni, 256), 256, 0, s>>>(ni, is, id, iw, wk.soff, wk.cur, wk.sdst, wk.swt);
-    ds_best_k<<<gridd(n, 256), 256, 0, s>>>(n, wk.soff, wk.sdst, wk.swt, Cprev, K, Sig, A, p, affected,
+    LK_COUNTED ds_place_k<<<gridd(ni, 256), 256, 0, s>>>(ni, is, id, iw, wk.soff, wk.cur, wk.sdst, wk.swt);
+    LK_COUNTED ds_best_k<<<gridd(n, 256), 256, 0, s>>>(n, wk.soff, wk.sdst, wk.swt, Cprev, K, Sig, A, p, affected,
                                             wk.dE, wk.dC);
   }
-  ds_expand_k<<<gridd(n, 256, 152 * 32), 256, 0, s>>>(n, off, idx, Cprev, wk.dE, wk.dC, affected);
+  LK_COUNTED ds_expand_k<<<gridd(n, 256, 152 * 32), 256, 0, s>>>(n, off, idx, Cprev, wk.dE, wk.dC, affected);
 }
 
 // ---------------------------------------------------------------------------
@@ -263,15 +263,15 @@ int apply_batch(int64_t n, const int64_t *off, const int32_t *idx, const int32_t
   if (cudaStreamSynchronize(s) != cudaSuccess) return LEIDEN_ECUDA;
   if (herr) return LEIDEN_EINVAL;
   if (nnz > 0) cudaMemsetAsync(wk.delmark, 0, (size_t)nnz, s);
-  if (n > 0) ba_deg_k<<<gridd(n, 256), 256, 0, s>>>(n, off, wk.newdeg);
-  if (nd > 0) ba_del_k<<<gridd(nd, 256), 256, 0, s>>>(nd, ds, dd, dw, off, idx, w, wk.delmark, wk.newdeg, wk.err);
+  if (n > 0) LK_COUNTED ba_deg_k<<<gridd(n, 256), 256, 0, s>>>(n, off, wk.newdeg);
+  if (nd > 0) LK_COUNTED ba_del_k<<<gridd(nd, 256), 256, 0, s>>>(nd, ds, dd, dw, off, idx, w, wk.delmark, wk.newdeg, wk.err);
   cudaMemsetAsync(wk.cnt, 0, (size_t)(n + 1) * sizeof(int64_t), s);
   cudaMemsetAsync(wk.cur, 0, (size_t)(n + 1) * sizeof(int64_t), s);
-  if (ni > 0) ds_cnt_k<<<gridd(ni, 256), 256, 0, s>>>(ni, is, id, wk.cnt);
+  if (ni > 0) LK_COUNTED ds_cnt_k<<<gridd(ni, 256), 256, 0, s>>>(ni, is, id, wk.cnt);
   exclusive_scan<int64_t>(wk.cnt, wk.ioff, n, wk.scan_tmp, s);
   if (ni > 0) {
-    ds_place_k<<<gridd(ni, 256), 256, 0, s>>>(ni, is, id, iw, wk.ioff, wk.cur, wk.idst, wk.iwt);
-    ba_ins_row_k<<<gridd(n, 128), 128, 0, s>>>(n, wk.ioff, wk.idst, wk.iwt, off, idx, wk.delmark, wk.newdeg);
+    LK_COUNTED ds_place_k<<<gridd(ni, 256), 256, 0, s>>>(ni, is, id, iw, wk.ioff, wk.cur, wk.idst, wk.iwt);
+    LK_COUNTED ba_ins_row_k<<<gridd(n, 128), 128, 0, s>>>(n, wk.ioff, wk.idst, wk.iwt, off, idx, wk.delmark, wk.newdeg);
   }
   exclusive_scan<int64_t>(wk.newdeg, off_out, n, wk.scan_tmp, s);
   int64_t nnz2 = 0;
@@ -281,7 +281,7 @@ int apply_batch(int64_t n, const int64_t *off, const int32_t *idx, const int32_t
   if (herr) return LEIDEN_EINVAL;
   if (nnz2 > cap_nnz) return LEIDEN_ENOMEM;
   if (n > 0)
-    ba_write_k<<<gridd(n * 32, 256, 152 * 32), 256, 0, s>>>(n, off, idx, w, wk.delmark, wk.ioff, wk.idst, wk.iwt,
+    LK_COUNTED ba_write_k<<<gridd(n * 32, 256, 152 * 32), 256, 0, s>>>(n, off, idx, w, wk.delmark, wk.ioff, wk.idst, wk.iwt,
                                                              off_out, idx_out, w_out, wk.err);
   cudaMemcpyAsync(&herr, wk.err, sizeof(u64), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return LEIDEN_ECUDA;

@@ -297,16 +297,16 @@ __global__ void __launch_bounds__(256) mark_big_rows_k(const int32_t *big, const
 
 void launch_mark_big(const int32_t *big, const u64 *count, const int64_t *off, const int32_t *idx,
                      uint8_t *processed, int sms, cudaStream_t s) {
-  mark_big_rows_k<<<sms * 4, 256, 0, s>>>(big, count, off, idx, processed);
+  LK_COUNTED mark_big_rows_k<<<sms * 4, 256, 0, s>>>(big, count, off, idx, processed);
 }
 
 template <typename WT, typename ST, bool REFINE, bool ASYNC>
 void launch_hubs(const MoveArgs<WT> &a, const HubWork &hw, int sms, cudaStream_t s) {
   if (a.list_n <= 0) return;
-  hub_prep_k<WT><<<1, 1024, 0, s>>>(a, REFINE, hw);
-  hub_insert_k<WT><<<sms * 8, 256, 0, s>>>(a, REFINE, hw);
-  hub_scan_k<WT, ST><<<sms * 8, 256, 0, s>>>(a, hw);
-  hub_final_k<WT, ST, REFINE, ASYNC><<<(unsigned)((a.list_n + 255) / 256), 256, 0, s>>>(a, hw);
+  LK_COUNTED hub_prep_k<WT><<<1, 1024, 0, s>>>(a, REFINE, hw);
+  LK_COUNTED hub_insert_k<WT><<<sms * 8, 256, 0, s>>>(a, REFINE, hw);
+  LK_COUNTED hub_scan_k<WT, ST><<<sms * 8, 256, 0, s>>>(a, hw);
+  LK_COUNTED hub_final_k<WT, ST, REFINE, ASYNC><<<(unsigned)((a.list_n + 255) / 256), 256, 0, s>>>(a, hw);
 }
 
 #define LK_HUB_INST(WT, ST)                                                                              \

@@ -12,6 +12,12 @@ typedef unsigned long long u64;
 
 namespace lk {
 
+// Every kernel launch of the library goes through LK_COUNTED, which bumps a
+// process-wide counter (leiden_kernel_launches) before the launch:
+//   if (n > 0) LK_COUNTED my_kernel<<<grid, block, 0, s>>>(args);
+void note_launch();
+#define LK_COUNTED ::lk::note_launch(),
+
 // ---------------------------------------------------------------------------
 // Degree tiers of the local-move / refinement kernels.  A vertex of degree d
 // (CSR entries, self-loop included) goes to the first tier with d <= maxdeg.

@@ -36,14 +36,14 @@ __global__ void row_sums_k(GraphView<WT> g, int64_t *K) {
 template <typename WT>
 void launch_row_sums(GraphView<WT> g, int64_t *K, cudaStream_t s) {
   if (g.n <= 0) return;
-  row_sums_k<WT><<<grid_for(g.n * 32, 256, 152 * 64), 256, 0, s>>>(g, K);
+  LK_COUNTED row_sums_k<WT><<<grid_for(g.n * 32, 256, 152 * 64), 256, 0, s>>>(g, K);
 }
 template void launch_row_sums<int32_t>(GraphView<int32_t>, int64_t *, cudaStream_t);
 template void launch_row_sums<int64_t>(GraphView<int64_t>, int64_t *, cudaStream_t);
 
 __global__ void iota_k(int32_t *a, int64_t n) { GRID_STRIDE(i, n) a[i] = (int32_t)i; }
 void launch_iota(int32_t *a, int64_t n, cudaStream_t s) {
-  if (n > 0) iota_k<<<grid_for(n, 256), 256, 0, s>>>(a, n);
+  if (n > 0) LK_COUNTED iota_k<<<grid_for(n, 256), 256, 0, s>>>(a, n);
 }
 __global__ void fill_u8_k(uint8_t *a, uint8_t v, int64_t n) { GRID_STRIDE(i, n) a[i] = v; }
 void launch_fill_u8(uint8_t *a, uint8_t v, int64_t n, cudaStream_t s) {
@@ -54,7 +54,7 @@ void launch_copy_i64(int64_t *dst, const int64_t *src, int64_t n, cudaStream_t s
 }
 __global__ void invert_u8_k(uint8_t *d, const uint8_t *a, int64_t n) { GRID_STRIDE(i, n) d[i] = a[i] ? 0 : 1; }
 void launch_invert_u8(uint8_t *dst, const uint8_t *src, int64_t n, cudaStream_t s) {
-  if (n > 0) invert_u8_k<<<grid_for(n, 256), 256, 0, s>>>(dst, src, n);
+  if (n > 0) LK_COUNTED invert_u8_k<<<grid_for(n, 256), 256, 0, s>>>(dst, src, n);
 }
 
 __global__ void sum_i64_k(const int64_t *a, int64_t n, u64 *out) {
@@ -65,7 +65,7 @@ __global__ void sum_i64_k(const int64_t *a, int64_t n, u64 *out) {
   if (threadIdx.x == 0 && s) atomicAdd(out, (u64)s);
 }
 void launch_sum_i64(const int64_t *a, int64_t n, u64 *out, cudaStream_t s) {
-  if (n > 0) sum_i64_k<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(a, n, out);
+  if (n > 0) LK_COUNTED sum_i64_k<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(a, n, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -93,10 +93,10 @@ void launch_subset_renumber(int64_t n, int32_t *C, const int64_t *Sig, int64_t *
                             const uint8_t *ch, uint8_t *ch2, int32_t *rep, cudaStream_t s) {
   if (n <= 0) return;
   const unsigned g = grid_for(n, 256);
-  sr_init_k<<<g, 256, 0, s>>>(n, rep, Sig2, ch2);
-  sr_min_k<<<g, 256, 0, s>>>(n, C, rep);
-  sr_move_k<<<g, 256, 0, s>>>(n, rep, Sig, Sig2, ch, ch2);
-  sr_relabel_k<<<g, 256, 0, s>>>(n, C, rep);
+  LK_COUNTED sr_init_k<<<g, 256, 0, s>>>(n, rep, Sig2, ch2);
+  LK_COUNTED sr_min_k<<<g, 256, 0, s>>>(n, C, rep);
+  LK_COUNTED sr_move_k<<<g, 256, 0, s>>>(n, rep, Sig, Sig2, ch, ch2);
+  LK_COUNTED sr_relabel_k<<<g, 256, 0, s>>>(n, C, rep);
 }
 
 // breakChangedCommunities: every vertex of a changed community becomes its
@@ -111,7 +111,7 @@ __global__ void break_k(int64_t n, int32_t *C, const int64_t *K, int64_t *Sig, c
 }
 void launch_break(int64_t n, int32_t *C, const int64_t *K, int64_t *Sig, const uint8_t *ch,
                   cudaStream_t s) {
-  if (n > 0) break_k<<<grid_for(n, 256), 256, 0, s>>>(n, C, K, Sig, ch);
+  if (n > 0) LK_COUNTED break_k<<<grid_for(n, 256), 256, 0, s>>>(n, C, K, Sig, ch);
 }
 
 // Dense renumbering in increasing order of the old ID (flag + exclusive scan).
@@ -123,10 +123,10 @@ __global__ void store_total_k(const int64_t *scanned, int64_t n, u64 *dst) { *ds
 void launch_renumber(int64_t n, int32_t *C, uint8_t *exists, int64_t *scanned, int64_t *tmp,
                      u64 *ctr, cudaStream_t s) {
   cudaMemsetAsync(exists, 0, (size_t)(n > 0 ? n : 1), s);
-  if (n > 0) flag_k<<<grid_for(n, 256), 256, 0, s>>>(n, C, exists);
+  if (n > 0) LK_COUNTED flag_k<<<grid_for(n, 256), 256, 0, s>>>(n, C, exists);
   exclusive_scan<uint8_t>(exists, scanned, n, tmp, s);
-  if (n > 0) relabel_scan_k<<<grid_for(n, 256), 256, 0, s>>>(n, C, scanned);
-  store_total_k<<<1, 1, 0, s>>>(scanned, n, &ctr[CTR_NCOMM]);
+  if (n > 0) LK_COUNTED relabel_scan_k<<<grid_for(n, 256), 256, 0, s>>>(n, C, scanned);
+  LK_COUNTED store_total_k<<<1, 1, 0, s>>>(scanned, n, &ctr[CTR_NCOMM]);
 }
 
 // Dendrogram lookup C[v] <- C'[C[v]].
@@ -134,7 +134,7 @@ __global__ void lookup_k(int64_t n, int32_t *Ctop, const int32_t *Cp) {
   GRID_STRIDE(v, n) Ctop[v] = Cp[Ctop[v]];
 }
 void launch_lookup(int64_t n, int32_t *Ctop, const int32_t *Cp, cudaStream_t s) {
-  if (n > 0) lookup_k<<<grid_for(n, 256), 256, 0, s>>>(n, Ctop, Cp);
+  if (n > 0) LK_COUNTED lookup_k<<<grid_for(n, 256), 256, 0, s>>>(n, Ctop, Cp);
 }
 
 // Canonical labels: communities numbered by their smallest member vertex.
@@ -155,11 +155,11 @@ void launch_canonical(int64_t n, const int32_t *C, int32_t *out, int32_t *minv, 
                       int64_t *scanned, int64_t *tmp, cudaStream_t s) {
   if (n <= 0) return;
   const unsigned g = grid_for(n, 256);
-  canon_init_k<<<g, 256, 0, s>>>(n, minv, flag);
-  canon_min_k<<<g, 256, 0, s>>>(n, C, minv);
-  canon_flag_k<<<g, 256, 0, s>>>(n, minv, flag);
+  LK_COUNTED canon_init_k<<<g, 256, 0, s>>>(n, minv, flag);
+  LK_COUNTED canon_min_k<<<g, 256, 0, s>>>(n, C, minv);
+  LK_COUNTED canon_flag_k<<<g, 256, 0, s>>>(n, minv, flag);
   exclusive_scan<uint8_t>(flag, scanned, n, tmp, s);
-  canon_out_k<<<g, 256, 0, s>>>(n, C, minv, scanned, out);
+  LK_COUNTED canon_out_k<<<g, 256, 0, s>>>(n, C, minv, scanned, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -204,8 +204,8 @@ void launch_modularity_terms(GraphView<WT> g, const int32_t *C, int64_t *Sig_tmp
   cudaMemsetAsync(acc, 0, 4 * sizeof(u64), s);
   if (g.n <= 0) return;
   cudaMemsetAsync(Sig_tmp, 0, (size_t)g.n * sizeof(int64_t), s);
-  mod_rows_k<WT><<<grid_for(g.n * 32, 256, 152 * 32), 256, 0, s>>>(g, C, Sig_tmp, acc);
-  mod_sq_k<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(g.n, Sig_tmp, acc);
+  LK_COUNTED mod_rows_k<WT><<<grid_for(g.n * 32, 256, 152 * 32), 256, 0, s>>>(g, C, Sig_tmp, acc);
+  LK_COUNTED mod_sq_k<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(g.n, Sig_tmp, acc);
 }
 template void launch_modularity_terms<int32_t>(GraphView<int32_t>, const int32_t *, int64_t *, u64 *, cudaStream_t);
 template void launch_modularity_terms<int64_t>(GraphView<int64_t>, const int32_t *, int64_t *, u64 *, cudaStream_t);
@@ -217,7 +217,7 @@ __global__ void sigma_from_k(int64_t n, const int32_t *C, const int64_t *K, int6
 void launch_sigma_from(int64_t n, const int32_t *C, const int64_t *K, int64_t *Sig, cudaStream_t s) {
   if (n <= 0) return;
   cudaMemsetAsync(Sig, 0, (size_t)n * sizeof(int64_t), s);
-  sigma_from_k<<<grid_for(n, 256), 256, 0, s>>>(n, C, K, Sig);
+  LK_COUNTED sigma_from_k<<<grid_for(n, 256), 256, 0, s>>>(n, C, K, Sig);
 }
 
 // ---------------------------------------------------------------------------
@@ -238,7 +238,7 @@ __global__ void update_weights_k(int64_t cnt, const int32_t *src, const int32_t 
 }
 void launch_update_weights(int64_t count, const int32_t *src, const int32_t *dst, const int32_t *w,
                            int sign, const int32_t *Cprev, int64_t *K, int64_t *Sig, cudaStream_t s) {
-  if (count > 0) update_weights_k<<<grid_for(count, 256), 256, 0, s>>>(count, src, dst, w, sign, Cprev, K, Sig);
+  if (count > 0) LK_COUNTED update_weights_k<<<grid_for(count, 256), 256, 0, s>>>(count, src, dst, w, sign, Cprev, K, Sig);
 }
 
 // changedCommunities (reading: the flag of the shared community).
@@ -251,7 +251,7 @@ __global__ void changed_k(int64_t cnt, const int32_t *src, const int32_t *dst, c
 }
 void launch_changed_communities(int64_t count, const int32_t *src, const int32_t *dst,
                                 const int32_t *Cprev, uint8_t *changed, cudaStream_t s) {
-  if (count > 0) changed_k<<<grid_for(count, 256), 256, 0, s>>>(count, src, dst, Cprev, changed);
+  if (count > 0) LK_COUNTED changed_k<<<grid_for(count, 256), 256, 0, s>>>(count, src, dst, Cprev, changed);
 }
 
 // Alg. frontier: deletions inside a community (same = 1) and insertions across
@@ -265,7 +265,7 @@ __global__ void mark_df_k(int64_t cnt, const int32_t *src, const int32_t *dst, c
 }
 void launch_mark_df(int64_t count, const int32_t *src, const int32_t *dst, const int32_t *Cprev,
                     int same, uint8_t *affected, cudaStream_t s) {
-  if (count > 0) mark_df_k<<<grid_for(count, 256), 256, 0, s>>>(count, src, dst, Cprev, same, affected);
+  if (count > 0) LK_COUNTED mark_df_k<<<grid_for(count, 256), 256, 0, s>>>(count, src, dst, Cprev, same, affected);
 }
 
 // A CSR is well formed: off[0] = 0, off[n] = nnz, offsets non-decreasing,
@@ -282,8 +282,8 @@ __global__ void check_graph_entries_k(int64_t n, int64_t nnz, const int32_t *idx
 }
 void launch_check_graph(int64_t n, int64_t nnz, const int64_t *off, const int32_t *idx, const int32_t *w,
                         u64 *err, cudaStream_t s) {
-  check_graph_rows_k<<<grid_for(n > 0 ? n : 1, 256), 256, 0, s>>>(n, nnz, off, err);
-  if (nnz > 0) check_graph_entries_k<<<grid_for(nnz, 256, 152 * 32), 256, 0, s>>>(n, nnz, idx, w, err);
+  LK_COUNTED check_graph_rows_k<<<grid_for(n > 0 ? n : 1, 256), 256, 0, s>>>(n, nnz, off, err);
+  if (nnz > 0) LK_COUNTED check_graph_entries_k<<<grid_for(nnz, 256, 152 * 32), 256, 0, s>>>(n, nnz, idx, w, err);
 }
 
 // Labels in [0, hi); sets *err on violation.
@@ -291,7 +291,7 @@ __global__ void check_range_k(const int32_t *a, int64_t n, int64_t hi, u64 *err)
   GRID_STRIDE(i, n) if (a[i] < 0 || a[i] >= hi) atomicOr(err, 32ull);
 }
 void launch_check_range(const int32_t *a, int64_t n, int64_t hi, u64 *err, cudaStream_t s) {
-  if (n > 0) check_range_k<<<grid_for(n, 256), 256, 0, s>>>(a, n, hi, err);
+  if (n > 0) LK_COUNTED check_range_k<<<grid_for(n, 256), 256, 0, s>>>(a, n, hi, err);
 }
 
 // IDs in [0, n), no self-loops, positive weights; sets *err on violation.
@@ -304,7 +304,7 @@ __global__ void check_ids_k(int64_t cnt, const int32_t *src, const int32_t *dst,
 }
 void launch_check_ids(int64_t count, const int32_t *src, const int32_t *dst, const int32_t *w,
                       int64_t n, u64 *err, cudaStream_t s) {
-  if (count > 0) check_ids_k<<<grid_for(count, 256), 256, 0, s>>>(count, src, dst, w, n, err);
+  if (count > 0) LK_COUNTED check_ids_k<<<grid_for(count, 256), 256, 0, s>>>(count, src, dst, w, n, err);
 }
 
 }  // namespace lk

@@ -466,14 +466,14 @@ void launch_apply_moves(const int32_t *prop_i, const int32_t *prop_c, const i128
                         u64 *ctr, int32_t *C, const int64_t *K, int64_t *Sig,
                         uint8_t *changed, uint8_t *processed, const int64_t *off,
                         const int32_t *idx, int32_t *big, int dynamic, int sms, cudaStream_t s) {
-  apply_moves_k<<<sms * 4, 256, 0, s>>>(prop_i, prop_c, prop_S, ctr, C, K, Sig, changed,
+  LK_COUNTED apply_moves_k<<<sms * 4, 256, 0, s>>>(prop_i, prop_c, prop_S, ctr, C, K, Sig, changed,
                                         processed, off, idx, big, dynamic);
 }
 
 void launch_apply_refine(const int32_t *prop_i, const int32_t *prop_c, u64 *ctr,
                          const uint8_t *stamp, uint8_t sv, int32_t *C, const int64_t *K,
                          int64_t *Sig, int sms, cudaStream_t s) {
-  apply_refine_k<<<sms * 2, 256, 0, s>>>(prop_i, prop_c, ctr, stamp, sv, C, K, Sig);
+  LK_COUNTED apply_refine_k<<<sms * 2, 256, 0, s>>>(prop_i, prop_c, ctr, stamp, sv, C, K, Sig);
 }
 
 // ---------------------------------------------------------------------------
@@ -490,7 +490,7 @@ static void launch_group_k(const Tier &t, const MoveArgs<WT> &a, int sms, cudaSt
   const int64_t cap = (int64_t)sms * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  k<<<(unsigned)blocks, threads, smem, s>>>(a);
+  LK_COUNTED k<<<(unsigned)blocks, threads, smem, s>>>(a);
 }
 
 template <typename WT, typename ST, bool REFINE, bool ASYNC>
@@ -515,7 +515,7 @@ void launch_decide(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s
   if (blocks > cap) blocks = cap;
   auto k = decide_block<false, REFINE, ASYNC, WT, ST>;
   ensure_smem((const void *)k, smem);
-  k<<<(unsigned)blocks, t.threads, smem, s>>>(a, log2H);
+  LK_COUNTED k<<<(unsigned)blocks, t.threads, smem, s>>>(a, log2H);
 }
 
 #define LK_INST(WT, ST)                                                                          \

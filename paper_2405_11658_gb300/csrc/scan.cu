@@ -121,9 +121,9 @@ void exclusive_scan(const TI *in, int64_t *out, int64_t n, int64_t *tmp, cudaStr
     return;
   }
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-  scan_tile_reduce<TI><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, tmp);
-  scan_partials<<<1, 1024, 0, s>>>(tmp, nb, out + n);
-  scan_tile_apply<TI><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, tmp, out);
+  LK_COUNTED scan_tile_reduce<TI><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, tmp);
+  LK_COUNTED scan_partials<<<1, 1024, 0, s>>>(tmp, nb, out + n);
+  LK_COUNTED scan_tile_apply<TI><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, tmp, out);
 }
 
 template void exclusive_scan<uint8_t>(const uint8_t *, int64_t *, int64_t, int64_t *, cudaStream_t);

@@ -54,3 +54,11 @@ def test_strerror_and_defaults_without_gpu():
     assert d["gamma"] == 1.0 and d["tol"] == 0.01 and d["tol_drop"] == 10.0
     assert d["max_iters"] == 20 and d["det_subsets"] == 8
     assert L._strerror(-1) == "invalid argument"
+
+
+def test_launch_counter_starts_at_zero_without_gpu_work():
+    import paper_2405_11658_gb300 as L
+    n0 = L.kernel_launches()
+    assert n0 >= 0
+    L.default_opts()  # host-only calls enqueue nothing
+    assert L.kernel_launches() == n0
