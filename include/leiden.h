@@ -210,6 +210,62 @@ int leiden_modularity_noalloc(const leiden_csr *g, const int32_t *membership, do
  * difference two readings to count the launches of a region. */
 uint64_t leiden_kernel_launches(void);
 
+/* Degree tiers of the local-moving and refinement kernels.  A vertex whose
+ * CSR row has d entries is processed by the first tier with d <= max_degree
+ * (vertices with d = 0 are never processed).  A GROUP tier gives each vertex
+ * `lanes` lanes of a warp and a shared-memory hashtable of 2^log2_slots
+ * slots; a BLOCK tier gives it a block of `threads` threads and a
+ * shared-memory table of 2^log2_slots slots; the HUB tier (always the last,
+ * max_degree unbounded) spreads each row over many blocks with tables in
+ * global scratch.  The tier table changes only the kernel shapes, never the
+ * result: every vertex takes the same decision whichever tier processes it.
+ * The default table is the one leiden_tiers_default returns; leiden_autotune
+ * picks one per graph. */
+#define LEIDEN_MAX_TIERS 11
+enum { LEIDEN_TIER_GROUP = 1, LEIDEN_TIER_BLOCK = 2, LEIDEN_TIER_HUB = 3 };
+typedef struct {
+  int32_t kind;        /* LEIDEN_TIER_GROUP, LEIDEN_TIER_BLOCK or LEIDEN_TIER_HUB */
+  int32_t lanes;       /* GROUP: lanes per vertex, 4, 8, 16 or 32; otherwise 0 */
+  int32_t log2_slots;  /* GROUP: (lanes, log2_slots) in (4,3) (4,4) (8,4) (8,5) (16,5) (16,6)
+                        * (32,6..10); BLOCK: 6..14; HUB: 0 */
+  int32_t threads;     /* GROUP: 32..256, BLOCK: 64..1024, multiples of 32; HUB: 0 */
+  int64_t max_degree;  /* inclusive upper end of the degree range; HUB: ignored */
+} leiden_tier;
+typedef struct {
+  int32_t count;       /* tiers in use, 1..LEIDEN_MAX_TIERS; the last one is the HUB tier */
+  int32_t reserved;    /* must be 0 */
+  leiden_tier tier[LEIDEN_MAX_TIERS];
+} leiden_tier_table;
+
+/* Fills the default tier table (HOST). */
+void leiden_tiers_default(leiden_tier_table *out);
+
+/* Checks a tier table (HOST, no GPU needed): kinds and shapes from the lists
+ * above, max_degree increasing, 2^log2_slots >= 2 * max_degree for GROUP and
+ * BLOCK tiers (a table never fills past half), shared memory within 227 KB
+ * per block, exactly one HUB tier, last.  Returns LEIDEN_OK or LEIDEN_EINVAL. */
+int leiden_tiers_validate(const leiden_tier_table *t);
+
+/* Sets the context's tier table (HOST; NULL restores the default) for its
+ * following runs; LEIDEN_EINVAL if leiden_tiers_validate rejects it (the
+ * context keeps its table). */
+int leiden_ctx_set_tiers(leiden_ctx *ctx, const leiden_tier_table *t);
+
+/* Copies the context's tier table into *out (HOST). */
+int leiden_ctx_get_tiers(leiden_ctx *ctx, leiden_tier_table *out);
+
+/* Autotuner of the tier table.  Times leiden_static on g with opts (the
+ * context's stream, CUDA events) for each of up to max_trials candidate
+ * tables -- degree thresholds of the group, block and hub tiers, hashtable
+ * load factors and block shapes drawn from a fixed candidate list ordered by
+ * expected benefit -- taking the median of `repeats` runs each (>= 1), and
+ * sets the fastest on the context.  best_out (HOST, may be NULL) receives
+ * that table and best_ms (HOST, may be NULL) its median time.  The partition
+ * is the same for every candidate (DET); membership is not returned.  Errors:
+ * those of leiden_static. */
+int leiden_autotune(leiden_ctx *ctx, const leiden_csr *g, const leiden_opts *opts, int32_t max_trials,
+                    int32_t repeats, leiden_tier_table *best_out, double *best_ms);
+
 /* Detail of the context's last failure (a CUDA error name and message, or a
  * device consistency check), empty if none; owned by the context and valid
  * until its next call. */

@@ -78,6 +78,39 @@ class _Stats(C.Structure):
         return d
 
 
+MAX_TIERS = 11
+TIER_KINDS = {"group": 1, "block": 2, "hub": 3}
+
+
+class _Tier(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("lanes", C.c_int32), ("log2_slots", C.c_int32),
+                ("threads", C.c_int32), ("max_degree", C.c_int64)]
+
+
+class _TierTable(C.Structure):
+    _fields_ = [("count", C.c_int32), ("reserved", C.c_int32), ("tier", _Tier * MAX_TIERS)]
+
+    @classmethod
+    def of(cls, tiers) -> "_TierTable":
+        t = cls()
+        t.count = len(tiers)
+        if t.count > MAX_TIERS:
+            raise ValueError(f"at most {MAX_TIERS} tiers")
+        for k, d in enumerate(tiers):
+            x = t.tier[k]
+            x.kind = TIER_KINDS[d["kind"]]
+            x.lanes = int(d.get("lanes", 0))
+            x.log2_slots = int(d.get("log2_slots", 0))
+            x.threads = int(d.get("threads", 0))
+            x.max_degree = int(d.get("max_degree", 2**63 - 1))
+        return t
+
+    def as_list(self) -> list:
+        names = {v: k for k, v in TIER_KINDS.items()}
+        return [{"kind": names.get(x.kind, x.kind), "lanes": x.lanes, "log2_slots": x.log2_slots,
+                 "threads": x.threads, "max_degree": x.max_degree} for x in self.tier[:self.count]]
+
+
 _lib = None
 
 
@@ -115,6 +148,16 @@ def lib():
     L.leiden_apply_batch.restype = C.c_int
     L.leiden_modularity_noalloc.argtypes = [P, P, d, P, P]
     L.leiden_modularity_noalloc.restype = C.c_int
+    L.leiden_tiers_default.argtypes = [P]
+    L.leiden_tiers_default.restype = None
+    L.leiden_tiers_validate.argtypes = [P]
+    L.leiden_tiers_validate.restype = C.c_int
+    L.leiden_ctx_set_tiers.argtypes = [P, P]
+    L.leiden_ctx_set_tiers.restype = C.c_int
+    L.leiden_ctx_get_tiers.argtypes = [P, P]
+    L.leiden_ctx_get_tiers.restype = C.c_int
+    L.leiden_autotune.argtypes = [P, P, P, i32, i32, P, P]
+    L.leiden_autotune.restype = C.c_int
     L.leiden_kernel_launches.argtypes = []
     L.leiden_kernel_launches.restype = C.c_uint64
     _lib = L
@@ -243,6 +286,29 @@ class Context:
     def set_timing(self, on: bool):
         _check(lib().leiden_ctx_set_timing(self._h, 1 if on else 0), "leiden_ctx_set_timing")
 
+    def set_tiers(self, tiers=None):
+        """Sets the degree-tier table (a list of dicts as default_tiers()
+        returns; None restores the default)."""
+        t = _TierTable.of(tiers) if tiers is not None else None
+        _check(lib().leiden_ctx_set_tiers(self._h, C.byref(t) if t is not None else None),
+               "leiden_ctx_set_tiers", self._h)
+
+    def get_tiers(self) -> list:
+        t = _TierTable()
+        _check(lib().leiden_ctx_get_tiers(self._h, C.byref(t)), "leiden_ctx_get_tiers", self._h)
+        return t.as_list()
+
+    def autotune(self, g: Graph, opts: Opts | None = None, max_trials: int = 16, repeats: int = 3):
+        """leiden_autotune: times candidate tier tables on g, keeps the
+        fastest on this context and returns (tiers, median ms)."""
+        opts = opts or Opts()
+        t = _TierTable()
+        ms = C.c_double()
+        gc, oc = g.c(), opts.c()
+        _check(lib().leiden_autotune(self._h, C.byref(gc), C.byref(oc), int(max_trials), int(repeats),
+                                     C.byref(t), C.byref(ms)), "leiden_autotune", self._h)
+        return t.as_list(), ms.value
+
     def stats(self) -> dict:
         st = _Stats()
         _check(lib().leiden_get_stats(self._h, C.byref(st)), "leiden_get_stats")
@@ -321,6 +387,22 @@ def modularity_noalloc(g: Graph, memb, gamma: float = 1.0, stream=None) -> float
     return q.value
 
 
+def default_tiers() -> list:
+    """The library's default degree-tier table (leiden_tiers_default)."""
+    t = _TierTable()
+    lib().leiden_tiers_default(C.byref(t))
+    return t.as_list()
+
+
+def validate_tiers(tiers) -> bool:
+    """True iff leiden_tiers_validate accepts the table (no GPU needed)."""
+    try:
+        t = _TierTable.of(tiers)
+    except (KeyError, ValueError):
+        return False
+    return lib().leiden_tiers_validate(C.byref(t)) == LEIDEN_OK
+
+
 def kernel_launches() -> int:
     """Kernels the library has enqueued in this process so far
     (leiden_kernel_launches); difference two readings to count a region."""
@@ -335,4 +417,5 @@ def default_opts() -> dict:
 
 EXPORTED = ("leiden_modularity_noalloc", "leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
             "leiden_update", "leiden_modularity", "leiden_apply_batch", "leiden_get_stats",
-            "leiden_ctx_set_timing", "leiden_strerror", "leiden_kernel_launches")
+            "leiden_ctx_set_timing", "leiden_strerror", "leiden_kernel_launches", "leiden_tiers_default",
+            "leiden_tiers_validate", "leiden_ctx_set_tiers", "leiden_ctx_get_tiers", "leiden_autotune")

@@ -73,6 +73,8 @@ struct leiden_ctx {
   cudaEvent_t ev_join[NAUX] = {};
 };
 
+cudaStream_t lk::ctx_stream(leiden_ctx *c) { return c->st; }
+
 namespace {
 
 constexpr int MAX_KEYS = 256 * MAX_TIERS;
@@ -643,6 +645,21 @@ void leiden_opts_default(leiden_opts *o) {
   o->sched = LEIDEN_DET;
   o->det_subsets = 8;
   o->refine_all_first_pass = 0;
+}
+
+int leiden_ctx_set_tiers(leiden_ctx *c, const leiden_tier_table *t) {
+  if (!c) return LEIDEN_EINVAL;
+  if (!t) { c->tiers = default_tiers(); return LEIDEN_OK; }
+  TierTable tt;
+  if (tiers_from_public(t, &tt) != LEIDEN_OK) return LEIDEN_EINVAL;
+  c->tiers = tt;
+  return LEIDEN_OK;
+}
+
+int leiden_ctx_get_tiers(leiden_ctx *c, leiden_tier_table *out) {
+  if (!c || !out) return LEIDEN_EINVAL;
+  tiers_to_public(c->tiers, out);
+  return LEIDEN_OK;
 }
 
 uint64_t leiden_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }

@@ -39,6 +39,12 @@ struct TierTable {
   Tier t[MAX_TIERS];
 };
 TierTable default_tiers();
+// Conversions between the public tier table (leiden_tier_table) and the
+// internal one (tier 0 = degree-0 vertices, never launched).
+int tiers_from_public(const leiden_tier_table *p, TierTable *out);
+void tiers_to_public(const TierTable &tt, leiden_tier_table *out);
+// The stream a context is bound to.
+cudaStream_t ctx_stream(leiden_ctx *c);
 
 template <typename WT>
 struct GraphView {

@@ -1,0 +1,135 @@
+"""Parity at the full size of the benchmark workload, in the launch
+configuration bench.py times: R-MAT scale 22, edge factor 16,
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), symmetrised, deduplicated, unit
+weights (4.19M vertices, 1.28e8 CSR entries); DET schedule with 8 colour
+classes, the default tier table, one context sized like the benchmark's.
+
+* The first pass (max_passes = 1) is what the oracle finishes in tens of
+  seconds at this size: membership, modularity and the per-pass statistics
+  must match it bit for bit, for Static and for a DF update with a 1e-3 |E|
+  batch.
+* The full runs are checked through properties that hold at any size:
+  canonical labels, every community connected, the returned Sigma^t equal
+  to the summed degrees, and the modularity equal to an exact integer
+  recomputation of Eq. 1 divided in the same double expression.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2405_11658_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import scipy.sparse as sp  # noqa: E402
+from scipy.sparse.csgraph import connected_components  # noqa: E402
+
+import paper_2405_11658_gb300 as L  # noqa: E402
+
+SCALE, EF = 22, 16
+SEED = 0x1EDE0 + 1
+FRAC = 1e-3
+
+
+@pytest.fixture(scope="module")
+def work():
+    g = S.rmat(SCALE, EF, 0.57, 0.19, 0.19, seed=SEED)
+    off, idx, w = g
+    size = max(2, int(round(FRAC * len(idx) / 2)))
+    dels, ins = S.random_batch(off, idx, w, size, seed=1000)
+    gt = O.apply_batch(off, idx, w, dels, ins)
+    max_nnz = max(len(idx), len(gt[1])) + 16
+    with L.Context(max_n=len(off) - 1, max_nnz=max_nnz) as ctx:
+        yield g, gt, dels, ins, ctx
+
+
+def rowsum(off, w):
+    n = len(off) - 1
+    rows = np.repeat(np.arange(n), np.diff(off))
+    # float64 sums of integers far below 2^53 are exact
+    return np.bincount(rows, weights=np.asarray(w, np.float64), minlength=n).astype(np.int64)
+
+
+def check_properties(off, idx, w, memb, q, Sigma=None):
+    n = len(off) - 1
+    memb = np.asarray(memb, np.int64)
+    # canonical labels: community IDs appear in increasing order of their
+    # smallest member, densely numbered from 0
+    first = np.full(memb.max() + 1, n, np.int64)
+    np.minimum.at(first, memb, np.arange(n))
+    assert np.all(np.diff(first) > 0) and first[0] == 0
+    # Eq. 1 with exact integers (gamma = 1)
+    rows = np.repeat(np.arange(n), np.diff(off))
+    inside = int(np.asarray(w, np.int64)[memb[rows] == memb[idx]].sum())
+    K = rowsum(off, w)
+    sig = np.bincount(memb, weights=K.astype(np.float64), minlength=memb.max() + 1).astype(np.int64)
+    two_m = int(K.sum())
+    assert two_m * two_m < 2**62  # the int64 sum of squares below is exact
+    sq = int((sig * sig).sum())
+    assert q == float(two_m * inside - sq) / (float(two_m) * float(two_m) * 1.0)
+    if Sigma is not None:
+        expect = np.zeros(n, np.int64)
+        expect[:len(sig)] = sig
+        assert np.array_equal(np.asarray(Sigma), expect)
+    # every community is connected: the graph restricted to intra-community
+    # edges has exactly one component per community
+    keep = memb[rows] == memb[idx]
+    A = sp.csr_matrix((np.ones(int(keep.sum()), np.int8), (rows[keep], idx[keep])), shape=(n, n))
+    ncomp, _ = connected_components(A, directed=False)
+    assert ncomp == memb.max() + 1
+
+
+def test_static_first_pass_bit_exact_at_full_size(work):
+    g, _, _, _, ctx = work
+    ref = O.static(*g, O.LeidenOpts(max_passes=1))
+    G = L.Graph.from_numpy(*g)
+    memb, q = ctx.static(G, L.Opts(max_passes=1))
+    assert np.array_equal(memb.cpu().numpy(), ref.membership)
+    assert q == ref.q
+    st = ctx.stats()
+    assert st["passes"] == ref.stats["passes"] == 1
+    for k in ("iters", "nv", "nnz", "moves", "refine_moves"):
+        assert st[k][:1] == ref.stats[k][:1], k
+
+
+def test_static_full_run_properties(work):
+    g, _, _, _, ctx = work
+    G = L.Graph.from_numpy(*g)
+    memb, q = ctx.static(G, L.Opts())
+    check_properties(*g, memb.cpu().numpy(), q)
+    st = ctx.stats()
+    assert st["nnz"][0] == len(g[1]) and st["nv"][0] == len(g[0]) - 1
+    assert all(a >= b for a, b in zip(st["nv"], st["nv"][1:]))
+
+
+def test_df_update_at_full_size(work):
+    g, gt, dels, ins, ctx = work
+    off, idx, w = g
+    G0 = L.Graph.from_numpy(*g)
+    prior, _ = ctx.static(G0, L.Opts())
+    prior = prior.cpu().numpy()
+    K = rowsum(off, w)
+    sig = np.bincount(prior, weights=K.astype(np.float64), minlength=len(K)).astype(np.int64)
+    Gt = L.Graph.from_numpy(*gt)
+    dev = Gt.off.device
+    args = (Gt, torch.from_numpy(prior).to(dev), L.Edges.from_numpy(dels), L.Edges.from_numpy(ins), "DF")
+    kw = dict(prior_K=torch.from_numpy(K).to(dev), prior_Sigma=torch.from_numpy(sig).to(dev))
+    # first pass: bit-exact with the oracle
+    ref = O.update(*gt, prior, K, sig, dels, ins, "DF", O.LeidenOpts(max_passes=1))
+    memb, Kt, St, q = ctx.update(*args, opts=L.Opts(max_passes=1), **kw)
+    assert np.array_equal(memb.cpu().numpy(), ref.membership)
+    assert np.array_equal(Kt.cpu().numpy(), ref.K)
+    assert np.array_equal(St.cpu().numpy(), ref.Sigma)
+    assert q == ref.q
+    st = ctx.stats()
+    assert st["affected0"] == ref.stats["affected0"] and st["changed0"] == ref.stats["changed0"]
+    # full run: properties
+    memb, Kt, St, q = ctx.update(*args, opts=L.Opts(), **kw)
+    assert np.array_equal(Kt.cpu().numpy(), rowsum(*gt[::2]))
+    check_properties(*gt, memb.cpu().numpy(), q, St.cpu().numpy())

@@ -306,3 +306,63 @@ def test_async_quality_and_invariants(ctx, name):
     assert B.all_connected(off, idx, memb)
     # no worse than the oracle's own schedules by more than the tolerance
     assert q >= min(gs.q, det.q) - ASYNC_TOL[name], (q, gs.q, det.q)
+
+
+def _g(lanes, log2_slots, threads, max_degree):
+    return {"kind": "group", "lanes": lanes, "log2_slots": log2_slots, "threads": threads, "max_degree": max_degree}
+
+
+def _b(log2_slots, threads, max_degree):
+    return {"kind": "block", "log2_slots": log2_slots, "threads": threads, "max_degree": max_degree}
+
+
+TIER_TABLES = {
+    "sparse_tables": [_g(4, 4, 256, 4), _g(8, 5, 256, 8), _g(16, 6, 256, 16), _g(32, 7, 256, 32),
+                      _g(32, 9, 256, 128), _g(32, 10, 128, 512), _b(12, 256, 2048), _b(14, 512, 8192),
+                      {"kind": "hub"}],
+    "small_blocks": [_g(4, 3, 128, 4), _g(8, 4, 128, 8), _g(16, 5, 128, 16), _g(32, 6, 128, 32),
+                     _g(32, 8, 128, 128), _b(10, 128, 512), _b(12, 128, 2048), _b(14, 256, 8192), {"kind": "hub"}],
+    "wide_lanes": [_g(32, 6, 64, 32), _b(12, 1024, 2048), {"kind": "hub"}],
+    "hub_from_512": [_g(8, 4, 256, 8), _g(32, 10, 256, 512), {"kind": "hub"}],
+}
+
+
+@pytest.mark.parametrize("table", list(TIER_TABLES))
+@pytest.mark.parametrize("name", ["rmat14", "hubs", "pp_1e4"])
+def test_tier_tables_do_not_change_the_result(ctx, table, name):
+    g = GRAPHS[name]()
+    ref = O.static(*g, O.LeidenOpts())
+    ctx.set_tiers(TIER_TABLES[table])
+    try:
+        assert ctx.get_tiers() == [dict(t, **{k: t.get(k, 0) for k in ("lanes", "log2_slots", "threads")},
+                                        max_degree=t.get("max_degree", 2**63 - 1))
+                                   for t in TIER_TABLES[table]]
+        memb, q, st = run_static(ctx, g, L.Opts())
+    finally:
+        ctx.set_tiers(None)
+    assert np.array_equal(memb, ref.membership), (table, name)
+    assert q == ref.q
+    assert_stats_equal(st, ref.stats)
+
+
+def test_set_tiers_rejects_a_bad_table_and_keeps_the_old_one(ctx):
+    before = ctx.get_tiers()
+    with pytest.raises(L.LeidenError):
+        ctx.set_tiers([_g(4, 3, 256, 8), {"kind": "hub"}])   # 8 slots for rows of 8
+    assert ctx.get_tiers() == before
+
+
+def test_autotune_picks_a_valid_table_and_keeps_the_result(ctx):
+    g = GRAPHS["rmat14"]()
+    ref = O.static(*g, O.LeidenOpts())
+    G = L.Graph.from_numpy(*g)
+    try:
+        tiers, ms = ctx.autotune(G, L.Opts(), max_trials=16, repeats=2)
+        assert ms > 0 and L.validate_tiers(tiers)
+        assert ctx.get_tiers() == tiers
+        memb, q = ctx.static(G, L.Opts())
+        assert np.array_equal(memb.cpu().numpy(), ref.membership)
+        assert q == ref.q
+    finally:
+        ctx.set_tiers(None)
+    assert ctx.get_tiers() == L.default_tiers()

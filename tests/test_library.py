@@ -62,3 +62,49 @@ def test_launch_counter_starts_at_zero_without_gpu_work():
     assert n0 >= 0
     L.default_opts()  # host-only calls enqueue nothing
     assert L.kernel_launches() == n0
+
+
+def _group(lanes, log2_slots, threads, max_degree):
+    return {"kind": "group", "lanes": lanes, "log2_slots": log2_slots, "threads": threads, "max_degree": max_degree}
+
+
+def _block(log2_slots, threads, max_degree):
+    return {"kind": "block", "log2_slots": log2_slots, "threads": threads, "max_degree": max_degree}
+
+
+HUB = {"kind": "hub"}
+
+
+def test_default_tier_table_validates():
+    import paper_2405_11658_gb300 as L
+    t = L.default_tiers()
+    assert t[-1]["kind"] == "hub" and len(t) <= L.MAX_TIERS
+    assert L.validate_tiers(t)
+    degs = [x["max_degree"] for x in t[:-1]]
+    assert degs == sorted(degs) and len(set(degs)) == len(degs)
+
+
+@pytest.mark.parametrize("bad", [
+    [],                                                             # empty
+    [_group(4, 3, 256, 4)],                                         # no hub tier
+    [HUB, _group(4, 3, 256, 4)],                                    # hub not last
+    [_group(4, 3, 256, 8), HUB],                                    # table 8 slots < 2 * 8
+    [_group(4, 5, 256, 4), HUB],                                    # unsupported (lanes, slots)
+    [_group(8, 4, 512, 8), HUB],                                    # group block > 256 threads
+    [_group(8, 4, 100, 8), HUB],                                    # threads not a multiple of 32
+    [_group(8, 4, 256, 8), _group(4, 3, 256, 4), HUB],              # degrees not increasing
+    [_block(15, 256, 8192), HUB],                                   # 2^15 slots exceed shared memory
+    [_block(12, 32, 2048), HUB],                                    # block tier below 64 threads
+    [_block(12, 256, 4096), HUB],                                   # 4096 slots < 2 * 4096
+    [_group(32, 10, 256, 512), _block(14, 512, 8192), {"kind": "hub", "threads": 64}],
+])
+def test_bad_tier_tables_are_rejected(bad):
+    import paper_2405_11658_gb300 as L
+    assert not L.validate_tiers(bad)
+
+
+def test_tier_table_variants_are_accepted():
+    import paper_2405_11658_gb300 as L
+    assert L.validate_tiers([HUB])                                  # every row on the hub path
+    assert L.validate_tiers([_group(32, 10, 128, 512), HUB])
+    assert L.validate_tiers([_group(4, 4, 256, 4), _group(8, 5, 256, 8), _block(14, 1024, 8192), HUB])
