@@ -204,9 +204,75 @@ int leiden_ctx_set_timing(leiden_ctx *ctx, int32_t enable);
 int leiden_modularity_noalloc(const leiden_csr *g, const int32_t *membership, double gamma,
                               void *cuda_stream, double *q_out);
 
+/* ---------------------------------------------------------------------------
+ * Many small graphs in one persistent launch.
+ *
+ * leiden_batch_run takes up to max_graphs graphs at once and runs, for each,
+ * the whole of Alg. leiden (every pass) inside one thread block: one kernel
+ * launch for the batch, whose blocks take graphs from a device-side queue
+ * (largest first) until none is left, with no host synchronisation between
+ * phases.  The launch, together with the upload of the graph descriptors and
+ * the download of the results, is captured once into a CUDA graph and
+ * replayed for every later batch.  Same arithmetic and DET schedule as
+ * leiden_static / leiden_update: for each graph the membership, modularity
+ * and per-pass statistics are bit-identical to those calls.  Meant for graphs
+ * small enough that one thread block per graph keeps the GPU busy; larger
+ * graphs belong to a leiden_ctx.  ND and DF updates recompute K^t and
+ * Sigma^t from G^t and C^{t-1} (Alg. update with no auxiliary input); DS is
+ * not offered here.
+ * ------------------------------------------------------------------------- */
+typedef struct leiden_batch leiden_batch;
+
+/* Creates a batch workspace bound to a stream (cudaStream_t as void*, NULL =
+ * legacy default stream) for up to max_graphs graphs per run with at most
+ * max_total_n vertices and max_total_nnz CSR entries summed over the run's
+ * graphs (about 300 B per vertex plus 36 B per entry).  `threads` is the
+ * block size of the persistent kernel (128..512, multiple of 32; 0 = 256)
+ * and blocks_per_sm the number of blocks per SM it is launched with (1..4;
+ * 0 = 2).  Errors: LEIDEN_EINVAL, LEIDEN_ENOMEM, LEIDEN_ECUDA. */
+int leiden_batch_create(leiden_batch **out, void *cuda_stream, int32_t max_graphs, int64_t max_total_n,
+                        int64_t max_total_nnz, int32_t threads, int32_t blocks_per_sm);
+
+/* Synchronises the stream and frees the workspace.  NULL is a no-op. */
+void leiden_batch_destroy(leiden_batch *b);
+
+enum { LEIDEN_STATIC = 0 };  /* leiden_batch_item.mode for Static Leiden */
+
+typedef struct {
+  leiden_csr g;              /* the graph (G^t for updates); DEVICE pointers */
+  int32_t mode;              /* LEIDEN_STATIC, LEIDEN_ND or LEIDEN_DF */
+  int32_t reserved;          /* must be 0 */
+  const int32_t *prior;      /* DEVICE [n]: C^{t-1}, labels in [0, n) (ND / DF) */
+  leiden_edges del, ins;     /* DEVICE: the batch that turned G^{t-1} into G^t (ND / DF) */
+  int32_t *membership_out;   /* DEVICE [n]: canonical labels */
+} leiden_batch_item;
+
+typedef struct {
+  int32_t status;            /* LEIDEN_OK, or this graph's error (EINVAL: malformed input,
+                              * EOVERFLOW: 2m >= 2^40, ECUDA: device consistency check) */
+  int32_t passes;            /* passes run */
+  double q;                  /* modularity (Eq. 1) at gamma of the returned membership */
+  int64_t affected0, changed0;
+  int32_t iters[LEIDEN_STATS_PASSES];
+  int64_t nv[LEIDEN_STATS_PASSES];
+  int64_t nnz[LEIDEN_STATS_PASSES];
+  int64_t moves[LEIDEN_STATS_PASSES];
+  int64_t refine_moves[LEIDEN_STATS_PASSES];
+} leiden_batch_result;
+
+/* Runs `count` graphs (items: HOST array) with opts (DET schedule only) and
+ * writes results[k] (HOST array) for each; returns LEIDEN_OK when the batch
+ * ran, even if some graphs report an error in their status.  The items'
+ * device buffers must stay valid until the call returns (it synchronises the
+ * stream).  Errors: LEIDEN_EINVAL (bad arguments, ASYNC schedule, a mode
+ * other than the three above), LEIDEN_ENOMEM (count or the summed sizes
+ * exceed the workspace), LEIDEN_ECUDA. */
+int leiden_batch_run(leiden_batch *b, int32_t count, const leiden_batch_item *items, const leiden_opts *opts,
+                     leiden_batch_result *results);
+
 /* Number of CUDA kernels this library has enqueued in this process so far,
- * over all contexts, devices and threads (a relaxed atomic counter; kernels
- * replayed from a captured CUDA graph count once, at capture).  Callers
+ * over all contexts, devices and threads (a relaxed atomic counter; every
+ * replay of a captured CUDA graph counts the kernels it runs).  Callers
  * difference two readings to count the launches of a region. */
 uint64_t leiden_kernel_launches(void);
 

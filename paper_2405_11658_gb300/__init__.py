@@ -111,6 +111,27 @@ class _TierTable(C.Structure):
                  "threads": x.threads, "max_degree": x.max_degree} for x in self.tier[:self.count]]
 
 
+class _BatchItem(C.Structure):
+    _fields_ = [("g", _Csr), ("mode", C.c_int32), ("reserved", C.c_int32), ("prior", C.c_void_p),
+                ("dels", _Edges), ("ins", _Edges), ("out", C.c_void_p)]
+
+
+class _BatchResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("passes", C.c_int32), ("q", C.c_double),
+                ("affected0", C.c_int64), ("changed0", C.c_int64),
+                ("iters", C.c_int32 * STATS_PASSES), ("nv", C.c_int64 * STATS_PASSES),
+                ("nnz", C.c_int64 * STATS_PASSES), ("moves", C.c_int64 * STATS_PASSES),
+                ("refine_moves", C.c_int64 * STATS_PASSES)]
+
+    def as_dict(self) -> dict:
+        k = min(self.passes, STATS_PASSES)
+        d = {"status": self.status, "passes": self.passes, "q": self.q, "affected0": self.affected0,
+             "changed0": self.changed0}
+        for name in ("iters", "nv", "nnz", "moves", "refine_moves"):
+            d[name] = list(getattr(self, name))[:k]
+        return d
+
+
 _lib = None
 
 
@@ -158,6 +179,12 @@ def lib():
     L.leiden_ctx_get_tiers.restype = C.c_int
     L.leiden_autotune.argtypes = [P, P, P, i32, i32, P, P]
     L.leiden_autotune.restype = C.c_int
+    L.leiden_batch_create.argtypes = [P, P, i32, i64, i64, i32, i32]
+    L.leiden_batch_create.restype = C.c_int
+    L.leiden_batch_destroy.argtypes = [P]
+    L.leiden_batch_destroy.restype = None
+    L.leiden_batch_run.argtypes = [P, i32, P, P, P]
+    L.leiden_batch_run.restype = C.c_int
     L.leiden_kernel_launches.argtypes = []
     L.leiden_kernel_launches.restype = C.c_uint64
     _lib = L
@@ -387,6 +414,69 @@ def modularity_noalloc(g: Graph, memb, gamma: float = 1.0, stream=None) -> float
     return q.value
 
 
+STATIC = 0
+
+
+class Batch:
+    """A ``leiden_batch``: many small graphs per call, each run whole by one
+    thread block of one persistent, CUDA-graph-captured launch."""
+
+    def __init__(self, max_graphs: int, max_total_n: int, max_total_nnz: int, threads: int = 0,
+                 blocks_per_sm: int = 0, stream=None):
+        torch = _torch()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = C.c_void_p()
+        _check(lib().leiden_batch_create(C.byref(self._h), C.c_void_p(self.stream.cuda_stream), int(max_graphs),
+                                         int(max_total_n), int(max_total_nnz), int(threads), int(blocks_per_sm)),
+               "leiden_batch_create")
+
+    def close(self):
+        if self._h:
+            lib().leiden_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def run(self, items, opts: Opts | None = None):
+        """items: list of dicts {"graph": Graph, "mode": "static" | "ND" | "DF",
+        "prior": tensor (updates), "dels": Edges, "ins": Edges, "out": tensor
+        (optional)}.  Returns (memberships, results): device tensors and one
+        dict per graph (status, q and per-pass statistics)."""
+        torch = _torch()
+        opts = opts or Opts()
+        arr = (_BatchItem * max(1, len(items)))()
+        outs = []
+        for k, it in enumerate(items):
+            g = it["graph"]
+            mode = it.get("mode", "static")
+            out = it.get("out")
+            if out is None:
+                out = torch.empty(g.n, dtype=torch.int32, device=g.off.device)
+            outs.append(out)
+            x = arr[k]
+            x.g = g.c()
+            x.mode = STATIC if mode == "static" else MODES[mode]
+            x.reserved = 0
+            x.prior = _ptr(it["prior"]) if it.get("prior") is not None else None
+            x.dels = it["dels"].c() if it.get("dels") is not None else _Edges(0, None, None, None)
+            x.ins = it["ins"].c() if it.get("ins") is not None else _Edges(0, None, None, None)
+            x.out = _ptr(out)
+        res = (_BatchResult * max(1, len(items)))()
+        oc = opts.c()
+        _check(lib().leiden_batch_run(self._h, len(items), arr, C.byref(oc), res), "leiden_batch_run")
+        return outs, [res[k].as_dict() for k in range(len(items))]
+
+
 def default_tiers() -> list:
     """The library's default degree-tier table (leiden_tiers_default)."""
     t = _TierTable()
@@ -418,4 +508,5 @@ def default_opts() -> dict:
 EXPORTED = ("leiden_modularity_noalloc", "leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
             "leiden_update", "leiden_modularity", "leiden_apply_batch", "leiden_get_stats",
             "leiden_ctx_set_timing", "leiden_strerror", "leiden_kernel_launches", "leiden_tiers_default",
-            "leiden_tiers_validate", "leiden_ctx_set_tiers", "leiden_ctx_get_tiers", "leiden_autotune")
+            "leiden_tiers_validate", "leiden_ctx_set_tiers", "leiden_ctx_get_tiers", "leiden_autotune",
+            "leiden_batch_create", "leiden_batch_destroy", "leiden_batch_run")

@@ -166,7 +166,8 @@ int check_opts(const leiden_opts *o, int64_t *p, int64_t *q, int *log2S) {
 
 int check_graph(leiden_ctx *c, const leiden_csr *g) {
   if (!g || g->n < 0 || g->nnz < 0 || g->n >= INT32_MAX) return LEIDEN_EINVAL;
-  if (g->n > 0 && (!g->off || (g->nnz > 0 && (!g->idx || !g->w)))) return LEIDEN_EINVAL;
+  // off has n + 1 entries even for an empty graph (the checks read off[0])
+  if (!g->off || (g->nnz > 0 && (!g->idx || !g->w))) return LEIDEN_EINVAL;
   if (g->n > c->max_n || g->nnz > c->max_nnz) return LEIDEN_ENOMEM;
   return LEIDEN_OK;
 }

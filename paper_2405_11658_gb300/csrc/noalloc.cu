@@ -52,7 +52,7 @@ extern "C" int leiden_modularity_noalloc(const leiden_csr *g, const int32_t *mem
                                          void *cuda_stream, double *q_out) {
   if (!g || !q_out || g->n < 0 || g->nnz < 0) return LEIDEN_EINVAL;
   if (g->n > LEIDEN_NOALLOC_MAX_N) return LEIDEN_ENOMEM;  // beyond the fixed scratch
-  if (g->n > 0 && (!g->off || !membership || (g->nnz > 0 && (!g->idx || !g->w)))) return LEIDEN_EINVAL;
+  if (!g->off || (g->n > 0 && !membership) || (g->nnz > 0 && (!g->idx || !g->w))) return LEIDEN_EINVAL;
   // gamma = p / q exactly, q = 2^20 before reduction
   const double scaled = gamma * 1048576.0;
   if (!(gamma > 0.0) || scaled > 9.0e15) return LEIDEN_EINVAL;
