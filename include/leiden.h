@@ -270,6 +270,105 @@ typedef struct {
 int leiden_batch_run(leiden_batch *b, int32_t count, const leiden_batch_item *items, const leiden_opts *opts,
                      leiden_batch_result *results);
 
+/* Device memory (bytes) a context's workspace holds (HOST out). */
+int leiden_ctx_device_bytes(leiden_ctx *ctx, int64_t *out);
+
+/* Device memory (bytes) a batch workspace holds (HOST out). */
+int leiden_batch_device_bytes(leiden_batch *b, int64_t *out);
+
+/* ---------------------------------------------------------------------------
+ * Serving: many graphs resident on the device, continuous batching of their
+ * update batches.
+ *
+ * A server keeps each admitted graph's CSR, membership and totals (K, Sigma)
+ * resident in device memory, admitted against a byte budget that also holds
+ * the server's own workspaces.  Update batches arrive at any time (from any
+ * thread) and are queued per graph, applied in arrival order: G^t is built
+ * from G^{t-1} and the batch (leiden_apply_batch), then C^t from C^{t-1} by
+ * the configured dynamic mode (DF by default).  Worker threads take work as
+ * soon as a graph and a worker are free, so requests that arrive while others
+ * run join the next launch instead of waiting for a batch boundary:
+ *   - graphs within the small limits go to one worker that runs every ready
+ *     small request in one persistent launch (leiden_batch_run);
+ *   - larger graphs go to `large_slots` workers, each with its own context and
+ *     stream, so their updates overlap on the device.
+ * Results are DET: each request's membership does not depend on what else
+ * ran beside it.
+ * ------------------------------------------------------------------------- */
+typedef struct leiden_server leiden_server;
+
+typedef struct {
+  int64_t hbm_budget;        /* bytes of device memory for workspaces and resident graphs */
+  int32_t large_slots;       /* concurrent workers for large graphs (>= 1) */
+  int32_t small_max_graphs;  /* graphs per persistent launch (>= 1) */
+  int64_t large_max_n;       /* largest graph a large worker's context holds */
+  int64_t large_max_nnz;
+  int64_t small_max_n;       /* a graph with n <= small_max_n and capacity <= small_max_nnz */
+  int64_t small_max_nnz;     /*   CSR entries runs on the persistent path */
+  int64_t small_batch_n;     /* vertices / entries summed over one persistent launch */
+  int64_t small_batch_nnz;
+  double growth;             /* spare CSR capacity of a resident graph, as a fraction of its nnz */
+  int32_t mode;              /* LEIDEN_DF (default when 0) or LEIDEN_ND */
+  int32_t reserved;          /* must be 0 */
+  leiden_opts opts;          /* DET schedule */
+} leiden_server_config;
+
+/* Fills a default configuration (HOST): 16 GB budget, 2 large slots, 64
+ * graphs per persistent launch, small graphs up to 2^17 vertices / 2^22
+ * entries, 25% growth, DF, default options. */
+void leiden_server_config_default(leiden_server_config *cfg);
+
+/* Creates a server on the current device and starts its workers.  Errors:
+ * LEIDEN_EINVAL, LEIDEN_ENOMEM (the workspaces exceed the budget), ECUDA. */
+int leiden_server_create(leiden_server **out, const leiden_server_config *cfg);
+
+/* Finishes the queued work, stops the workers, frees everything. */
+void leiden_server_destroy(leiden_server *s);
+
+/* Admits a graph (HOST CSR, copied to the device) if its footprint -- two
+ * CSR buffers of nnz * (1 + growth) entries, membership and totals -- fits
+ * the remaining budget, and queues its Static Leiden; *graph_id receives its
+ * handle and *request_id (may be NULL) the Static request.  Errors:
+ * LEIDEN_EINVAL (malformed sizes), LEIDEN_ENOMEM (over budget or too large
+ * for every worker). */
+int leiden_server_admit(leiden_server *s, int64_t n, int64_t nnz, const int64_t *off, const int32_t *idx,
+                        const int32_t *w, int32_t *graph_id, int64_t *request_id);
+
+/* Queues an update batch (HOST arrays in del / ins, copied) for a graph;
+ * *request_id receives its handle.  Errors: LEIDEN_EINVAL (unknown graph,
+ * bad sizes). */
+int leiden_server_submit(leiden_server *s, int32_t graph_id, const leiden_edges *del, const leiden_edges *ins,
+                         int64_t *request_id);
+
+typedef struct {
+  int32_t status;            /* LEIDEN_OK or the request's error */
+  int32_t graph;
+  int32_t path;              /* 0: persistent many-graph launch, 1: large-graph worker */
+  int32_t launch_graphs;     /* graphs in the same persistent launch (path 0) */
+  double q;                  /* modularity of the new membership */
+  double queue_ms;           /* submission to start of its work */
+  double latency_ms;         /* submission to result ready */
+  int64_t n, nnz;            /* of the graph after the request */
+} leiden_request_info;
+
+/* Waits up to timeout_ms (< 0: forever) for a request; LEIDEN_ETIMEOUT if it
+ * is not done by then.  *out (HOST) receives its record. */
+int leiden_server_wait(leiden_server *s, int64_t request_id, double timeout_ms, leiden_request_info *out);
+
+/* Copies a graph's current membership (n labels) into host_out, after
+ * waiting for its queued requests. */
+int leiden_server_membership(leiden_server *s, int32_t graph_id, int32_t *host_out, int64_t n);
+
+/* Waits for a graph's queued requests, then frees its device memory. */
+int leiden_server_evict(leiden_server *s, int32_t graph_id);
+
+typedef struct {
+  int64_t resident_graphs, resident_bytes, workspace_bytes, budget;
+  int64_t completed, failed, small_launches, small_graphs_launched, large_runs;
+} leiden_server_stats;
+
+int leiden_server_get_stats(leiden_server *s, leiden_server_stats *out);
+
 /* Number of CUDA kernels this library has enqueued in this process so far,
  * over all contexts, devices and threads (a relaxed atomic counter; every
  * replay of a captured CUDA graph counts the kernels it runs).  Callers

@@ -132,6 +132,25 @@ class _BatchResult(C.Structure):
         return d
 
 
+class _ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget", C.c_int64), ("large_slots", C.c_int32), ("small_max_graphs", C.c_int32),
+                ("large_max_n", C.c_int64), ("large_max_nnz", C.c_int64), ("small_max_n", C.c_int64),
+                ("small_max_nnz", C.c_int64), ("small_batch_n", C.c_int64), ("small_batch_nnz", C.c_int64),
+                ("growth", C.c_double), ("mode", C.c_int32), ("reserved", C.c_int32), ("opts", _Opts)]
+
+
+class _RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("graph", C.c_int32), ("path", C.c_int32), ("launch_graphs", C.c_int32),
+                ("q", C.c_double), ("queue_ms", C.c_double), ("latency_ms", C.c_double),
+                ("n", C.c_int64), ("nnz", C.c_int64)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [(name, C.c_int64) for name in ("resident_graphs", "resident_bytes", "workspace_bytes", "budget",
+                                                 "completed", "failed", "small_launches", "small_graphs_launched",
+                                                 "large_runs")]
+
+
 _lib = None
 
 
@@ -185,6 +204,28 @@ def lib():
     L.leiden_batch_destroy.restype = None
     L.leiden_batch_run.argtypes = [P, i32, P, P, P]
     L.leiden_batch_run.restype = C.c_int
+    L.leiden_server_config_default.argtypes = [P]
+    L.leiden_server_config_default.restype = None
+    L.leiden_server_create.argtypes = [P, P]
+    L.leiden_server_create.restype = C.c_int
+    L.leiden_server_destroy.argtypes = [P]
+    L.leiden_server_destroy.restype = None
+    L.leiden_server_admit.argtypes = [P, i64, i64, P, P, P, P, P]
+    L.leiden_server_admit.restype = C.c_int
+    L.leiden_server_submit.argtypes = [P, i32, P, P, P]
+    L.leiden_server_submit.restype = C.c_int
+    L.leiden_server_wait.argtypes = [P, i64, d, P]
+    L.leiden_server_wait.restype = C.c_int
+    L.leiden_server_membership.argtypes = [P, i32, P, i64]
+    L.leiden_server_membership.restype = C.c_int
+    L.leiden_server_evict.argtypes = [P, i32]
+    L.leiden_server_evict.restype = C.c_int
+    L.leiden_server_get_stats.argtypes = [P, P]
+    L.leiden_server_get_stats.restype = C.c_int
+    L.leiden_ctx_device_bytes.argtypes = [P, P]
+    L.leiden_ctx_device_bytes.restype = C.c_int
+    L.leiden_batch_device_bytes.argtypes = [P, P]
+    L.leiden_batch_device_bytes.restype = C.c_int
     L.leiden_kernel_launches.argtypes = []
     L.leiden_kernel_launches.restype = C.c_uint64
     _lib = L
@@ -477,6 +518,96 @@ class Batch:
         return outs, [res[k].as_dict() for k in range(len(items))]
 
 
+def _host_ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None and len(a) else None
+
+
+def _host_edges(b):
+    """(src, dst, w) numpy arrays as a leiden_edges of HOST pointers (the
+    arrays must outlive the call)."""
+    import numpy as np
+    if b is None:
+        return _Edges(0, None, None, None), None
+    arrs = tuple(np.ascontiguousarray(x, dtype=np.int32) for x in b)
+    return _Edges(len(arrs[0]), _host_ptr(arrs[0]), _host_ptr(arrs[1]), _host_ptr(arrs[2])), arrs
+
+
+class Server:
+    """A ``leiden_server``: resident graphs, HBM-budget admission and
+    continuous batching of update batches (host arrays in, host records out)."""
+
+    def __init__(self, opts: Opts | None = None, mode: str = "DF", **cfg):
+        c = _ServerConfig()
+        lib().leiden_server_config_default(C.byref(c))
+        for k, v in cfg.items():
+            if not hasattr(c, k):
+                raise TypeError(f"unknown server setting {k}")
+            setattr(c, k, v)
+        c.mode = MODES[mode]
+        if opts is not None:
+            c.opts = opts.c()
+        self._h = C.c_void_p()
+        _check(lib().leiden_server_create(C.byref(self._h), C.byref(c)), "leiden_server_create")
+
+    def close(self):
+        if self._h:
+            lib().leiden_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def admit(self, off, idx, w):
+        """Admits a host CSR; returns (graph_id, request_id of its Static run)."""
+        import numpy as np
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.int32)
+        gid, rid = C.c_int32(), C.c_int64()
+        _check(lib().leiden_server_admit(self._h, len(off) - 1, len(idx), _host_ptr(off), _host_ptr(idx),
+                                         _host_ptr(w), C.byref(gid), C.byref(rid)), "leiden_server_admit")
+        return gid.value, rid.value
+
+    def submit(self, graph_id: int, dels=None, ins=None) -> int:
+        d, keep_d = _host_edges(dels)
+        i, keep_i = _host_edges(ins)
+        rid = C.c_int64()
+        _check(lib().leiden_server_submit(self._h, int(graph_id), C.byref(d), C.byref(i), C.byref(rid)),
+               "leiden_server_submit")
+        del keep_d, keep_i
+        return rid.value
+
+    def wait(self, request_id: int, timeout_ms: float = -1.0) -> dict:
+        info = _RequestInfo()
+        _check(lib().leiden_server_wait(self._h, int(request_id), float(timeout_ms), C.byref(info)),
+               "leiden_server_wait")
+        return {name: getattr(info, name) for name, _ in info._fields_}
+
+    def membership(self, graph_id: int, n: int):
+        import numpy as np
+        out = np.empty(n, np.int32)
+        _check(lib().leiden_server_membership(self._h, int(graph_id), _host_ptr(out) if n else None, int(n)),
+               "leiden_server_membership")
+        return out
+
+    def evict(self, graph_id: int):
+        _check(lib().leiden_server_evict(self._h, int(graph_id)), "leiden_server_evict")
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib().leiden_server_get_stats(self._h, C.byref(st)), "leiden_server_get_stats")
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+
 def default_tiers() -> list:
     """The library's default degree-tier table (leiden_tiers_default)."""
     t = _TierTable()
@@ -509,4 +640,7 @@ EXPORTED = ("leiden_modularity_noalloc", "leiden_ctx_last_error", "leiden_opts_d
             "leiden_update", "leiden_modularity", "leiden_apply_batch", "leiden_get_stats",
             "leiden_ctx_set_timing", "leiden_strerror", "leiden_kernel_launches", "leiden_tiers_default",
             "leiden_tiers_validate", "leiden_ctx_set_tiers", "leiden_ctx_get_tiers", "leiden_autotune",
-            "leiden_batch_create", "leiden_batch_destroy", "leiden_batch_run")
+            "leiden_batch_create", "leiden_batch_destroy", "leiden_batch_run", "leiden_server_create",
+            "leiden_server_destroy", "leiden_server_admit", "leiden_server_submit", "leiden_server_wait",
+            "leiden_server_membership", "leiden_server_evict", "leiden_server_get_stats",
+            "leiden_server_config_default", "leiden_ctx_device_bytes", "leiden_batch_device_bytes")

@@ -30,6 +30,7 @@ struct leiden_ctx {
   int64_t max_n = 0, max_nnz = 0;
   TierTable tiers{};
   std::vector<void *> allocs;
+  int64_t device_bytes = 0;
   // vertex arrays
   int32_t *Ctop, *Cp, *CB, *rep;
   int64_t *Kp, *Sp, *S2, *K0, *Ktmp;
@@ -86,6 +87,7 @@ int dalloc(leiden_ctx *c, void **p, size_t bytes) {
     return LEIDEN_ENOMEM;
   }
   c->allocs.push_back(*p);
+  c->device_bytes += (int64_t)bytes;
   return LEIDEN_OK;
 }
 
@@ -660,6 +662,12 @@ int leiden_ctx_set_tiers(leiden_ctx *c, const leiden_tier_table *t) {
 int leiden_ctx_get_tiers(leiden_ctx *c, leiden_tier_table *out) {
   if (!c || !out) return LEIDEN_EINVAL;
   tiers_to_public(c->tiers, out);
+  return LEIDEN_OK;
+}
+
+int leiden_ctx_device_bytes(leiden_ctx *c, int64_t *out) {
+  if (!c || !out) return LEIDEN_EINVAL;
+  *out = c->device_bytes;
   return LEIDEN_OK;
 }
 

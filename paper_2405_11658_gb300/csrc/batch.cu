@@ -175,6 +175,12 @@ extern "C" void leiden_batch_destroy(leiden_batch *b) {
   delete b;
 }
 
+extern "C" int leiden_batch_device_bytes(leiden_batch *b, int64_t *out) {
+  if (!b || !out) return LEIDEN_EINVAL;
+  *out = b->arena_bytes + (int64_t)b->desc_bytes + (int64_t)b->res_bytes;
+  return LEIDEN_OK;
+}
+
 extern "C" int leiden_batch_run(leiden_batch *b, int32_t count, const leiden_batch_item *items,
                                 const leiden_opts *opts, leiden_batch_result *results) {
   if (!b || count < 0 || (count > 0 && (!items || !results))) return LEIDEN_EINVAL;
