@@ -309,7 +309,8 @@ typedef struct {
   int64_t small_batch_nnz;
   double growth;             /* spare CSR capacity of a resident graph, as a fraction of its nnz */
   int32_t mode;              /* LEIDEN_DF (default when 0) or LEIDEN_ND */
-  int32_t reserved;          /* must be 0 */
+  int32_t autotune_trials;   /* > 0: leiden_autotune each large graph at admission with this many
+                              * candidate tier tables and use its table for the graph's runs */
   leiden_opts opts;          /* DET schedule */
 } leiden_server_config;
 

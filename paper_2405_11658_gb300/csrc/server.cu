@@ -49,6 +49,8 @@ struct Resident {
   int64_t *K[2] = {}, *Sig[2] = {};
   int csr = 0, mem = 0;   // current CSR and membership buffers
   bool has_aux = false;   // K / Sigma of the current membership are valid
+  bool tuned = false;     // `tiers` picked by the autotuner for this graph
+  leiden_tier_table tiers{};
   bool busy = false;
   std::deque<Request *> queue;
   std::vector<void *> allocs;
@@ -156,9 +158,14 @@ void run_large(leiden_server *s, int k, Resident *g, Request *r) {
   info.path = 1;
   int rc = LEIDEN_OK;
   double q = 0.0;
+  leiden_ctx_set_tiers(ctx, g->tuned ? &g->tiers : nullptr);
   if (r->is_static) {
     leiden_csr c = csr_of(*g, g->csr, g->nnz);
-    rc = leiden_static(ctx, &c, &s->cfg.opts, g->C[g->mem], &q);
+    if (s->cfg.autotune_trials > 0) {
+      rc = leiden_autotune(ctx, &c, &s->cfg.opts, s->cfg.autotune_trials, 1, &g->tiers, nullptr);
+      g->tuned = rc == LEIDEN_OK;
+    }
+    if (!rc) rc = leiden_static(ctx, &c, &s->cfg.opts, g->C[g->mem], &q);
     if (!rc) g->has_aux = false;
   } else {
     rc = grow(s, s->large_stage[k], batch_words(*r));
@@ -360,7 +367,7 @@ extern "C" int leiden_server_create(leiden_server **out, const leiden_server_con
   leiden_server_config c = *cfg;
   if (c.mode == 0) c.mode = LEIDEN_DF;
   if (c.mode != LEIDEN_DF && c.mode != LEIDEN_ND) return LEIDEN_EINVAL;
-  if (c.large_slots < 1 || c.large_slots > 16 || c.small_max_graphs < 1 || c.reserved) return LEIDEN_EINVAL;
+  if (c.large_slots < 1 || c.large_slots > 16 || c.small_max_graphs < 1 || c.autotune_trials < 0) return LEIDEN_EINVAL;
   if (c.hbm_budget <= 0 || c.large_max_n < 1 || c.large_max_nnz < 1 || c.small_max_n < 1 || c.small_max_nnz < 1)
     return LEIDEN_EINVAL;
   if (c.small_batch_n < c.small_max_n || c.small_batch_nnz < c.small_max_nnz || !(c.growth >= 0.0))

@@ -107,8 +107,8 @@ def test_server_results_match_the_oracle_in_the_mix(expected):
 
 def test_server_result_alone_equals_result_in_the_mix(expected):
     graphs, seqs, want = expected
-    for k in (0, 5):
-        with L.Server(**CFG) as srv:
+    for k, trials in ((0, 0), (5, 0), (5, 3)):                # 3: the large graph's tier table autotuned
+        with L.Server(**dict(CFG, autotune_trials=trials)) as srv:
             gid, rid = srv.admit(*graphs[k])
             rids = [rid] + [srv.submit(gid, d, i) for d, i in seqs[k]]
             qs = [srv.wait(r)["q"] for r in rids]
