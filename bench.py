@@ -51,6 +51,15 @@ def parse():
     ap.add_argument("--sched", default="det", choices=["det", "async"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "serving"])
+    ap.add_argument("--serving-graphs", type=int, default=64)
+    ap.add_argument("--serving-max-n", type=float, default=1e7)
+    ap.add_argument("--serving-per-graph", type=int, default=10)
+    ap.add_argument("--serving-load", type=float, default=0.7)
+    ap.add_argument("--serving-slots", type=int, default=3)
+    ap.add_argument("--serving-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serving-autotune", type=int, default=0)
+    ap.add_argument("--serving-seed", type=int, default=5)
     return ap.parse_args()
 
 
@@ -345,10 +354,164 @@ def run_ours(args):
     return 0
 
 
+SERVING_METRIC = "serving: DF updates/s with p50/p99 per-batch latency, many resident graphs"
+
+
+def _serving_graph(job):
+    """Graph k of the serving workload and its update stream: log-spaced sizes
+    from 1e4 to max_n vertices (most of them small), planted-partition and
+    R-MAT alternating below 2e5 vertices and R-MAT above, edge factors 8 to
+    32 (8 above 1e6 vertices).  The stream holds batches of 1e-6..1e-3 |E|
+    (log-uniform): 80% insertions of pairs that are not edges of the graph,
+    20% deletions of distinct edges of the graph, so every batch stays valid
+    whatever ran before it."""
+    k, count, max_n, seed, per_graph = job
+    from paper_2405_11658_gb300 import synth as S
+    x = k / max(1, count - 1)
+    n = int(round(10 ** (4 + (np.log10(max_n) - 4) * x * x)))
+    ef = (8, 16, 32)[k % 3] if n <= 1_000_000 else 8
+    if n <= 200_000 and k % 2 == 0:
+        comms = max(4, n // 500)
+        g = S.planted_partition(n, comms, min(0.5, 2.0 * ef / (n / comms)), 0.1 * ef / n, seed + k)
+        kind = "pp"
+    else:
+        scale = max(10, int(round(np.log2(n))))
+        g = S.rmat(scale, ef, 0.57, 0.19, 0.19, seed=seed + k)
+        kind = f"rmat{scale}"
+    off, idx, w = g
+    n = len(off) - 1
+    eu, ev, ew = S.undirected_pairs(off, idx, w)
+    keys = np.sort(eu * n + ev)
+    rng = np.random.default_rng(seed * 1000 + k)
+    perm = rng.permutation(len(eu))
+    used = 0
+    stream = []
+    for _ in range(per_graph):
+        frac = 10 ** rng.uniform(-6, -3)
+        size = max(1, int(round(frac * len(eu))))
+        nd = size // 5
+        ni = size - nd
+        pick = perm[used:used + nd]
+        used += nd
+        dels = (eu[pick].astype(np.int32), ev[pick].astype(np.int32), ew[pick].astype(np.int32))
+        a = rng.integers(0, n, size=2 * ni + 16)
+        b = rng.integers(0, n, size=2 * ni + 16)
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        cand = lo * n + hi
+        pos = np.minimum(np.searchsorted(keys, cand), len(keys) - 1)
+        ok = (lo != hi) & (keys[pos] != cand)
+        cand = np.unique(cand[ok])[:ni]
+        ins = ((cand // n).astype(np.int32), (cand % n).astype(np.int32), np.ones(len(cand), np.int32))
+        stream.append((frac, dels, ins))
+    return kind, g, stream
+
+
+def serving_workload(count, max_n, seed, per_graph, procs):
+    """The graphs and streams, built by a pool of `procs` processes (spawned:
+    the caller has not touched the GPU yet)."""
+    import multiprocessing as mp
+    jobs = [(k, count, max_n, seed, per_graph) for k in range(count)]
+    if procs <= 1:
+        return [_serving_graph(j) for j in jobs]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_serving_graph, sorted(jobs, key=lambda j: -j[0]), chunksize=1)[::-1]
+
+
+def run_serving(args):
+    """Poisson arrivals of update batches over many resident graphs; prints
+    one JSON line (updates/s, p50 / p99 latency per path)."""
+    t0 = time.perf_counter()
+    work = serving_workload(args.serving_graphs, args.serving_max_n, 0x1EDE0 + 4, args.serving_per_graph + 1,
+                            min(16, os.cpu_count() or 1))
+    graphs = [(kind, g) for kind, g, _ in work]
+    streams = [st for _, _, st in work]
+    del work
+    gen_s = time.perf_counter() - t0
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2405_11658_gb300 as L
+    rng = np.random.default_rng(args.serving_seed)
+    small_max_n = 1 << 17
+    cfg = dict(hbm_budget=int(args.serving_budget_gb * (1 << 30)), large_slots=args.serving_slots,
+               small_max_graphs=64, large_max_n=max(len(g[0]) for _, g in graphs),
+               large_max_nnz=int(max(len(g[1]) for _, g in graphs) * 1.3) + 4096, small_max_n=small_max_n,
+               small_max_nnz=1 << 22, small_batch_n=1 << 22, small_batch_nnz=1 << 26, growth=0.05,
+               autotune_trials=args.serving_autotune)
+    with L.Server(**cfg) as srv:
+        ids, admit_rids = [], []
+        t_adm = time.perf_counter()
+        for _, g in graphs:
+            gid, rid = srv.admit(*g)
+            ids.append(gid)
+            admit_rids.append(rid)
+        for r in admit_rids:
+            info = srv.wait(r)
+            assert info["status"] == 0, info
+        admit_s = time.perf_counter() - t_adm
+        # calibration: one batch per graph, all at once
+        t_cal = time.perf_counter()
+        rids = [srv.submit(ids[k], *streams[k][0][1:]) for k in range(len(graphs))]
+        for r in rids:
+            srv.wait(r)
+        cal_s = time.perf_counter() - t_cal
+        mu = len(graphs) / cal_s
+        lam = args.serving_load * mu
+        # timed: Poisson arrivals at rate lam over a random graph order
+        order = [(k, j) for k in range(len(graphs)) for j in range(1, args.serving_per_graph + 1)]
+        rng.shuffle(order)
+        nxt = [1] * len(graphs)
+        submitted = []
+        launches0 = L.kernel_launches()
+        with Clocks(0) as clk:
+            t_start = time.perf_counter()
+            t_next = t_start
+            for k, _ in order:
+                t_next += rng.exponential(1.0 / lam)
+                delay = t_next - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                frac, dels, ins = streams[k][nxt[k]]
+                nxt[k] += 1
+                submitted.append((k, frac, srv.submit(ids[k], dels, ins)))
+            infos = [(k, frac, srv.wait(r)) for k, frac, r in submitted]
+            t_end = time.perf_counter()
+        launches = L.kernel_launches() - launches0
+        st = srv.stats()
+    ok = [x for x in infos if x[2]["status"] == 0]
+    lat = np.array([x[2]["latency_ms"] for x in ok])
+    per_path = {}
+    for path, name in ((0, "persistent"), (1, "large")):
+        v = np.array([x[2]["latency_ms"] for x in ok if x[2]["path"] == path])
+        if len(v):
+            per_path[name] = {"requests": int(len(v)), "p50_ms": float(np.percentile(v, 50)),
+                              "p99_ms": float(np.percentile(v, 99))}
+    launch_sizes = [x[2]["launch_graphs"] for x in ok if x[2]["path"] == 0]
+    line = {
+        "metric": SERVING_METRIC, "value": len(ok) / (t_end - t_start), "unit": "updates/s", "n_gpus": 1,
+        "steps": len(order), "warmup": len(graphs), "ms_per_step": 1000 * (t_end - t_start) / max(1, len(order)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"serving: {len(graphs)} resident graphs, 1e4..{args.serving_max_n:.0e} vertices, "
+                               f"Poisson DF update batches of 1e-6..1e-3 |E|",
+                   "graphs": [f"{kind}:{len(g[0]) - 1}:{len(g[1])}" for kind, g in graphs],
+                   "arrival_rate_per_s": lam, "load": args.serving_load, "large_slots": args.serving_slots,
+                   "budget_gb": args.serving_budget_gb, "autotune_trials": args.serving_autotune},
+        "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+        "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+        "paths": per_path, "failed": len(infos) - len(ok),
+        "mean_graphs_per_persistent_launch": float(np.mean(launch_sizes)) if launch_sizes else None,
+        "server": st, "gpu_launches": launches, "clocks": clk.summary(),
+        "gen_s": gen_s, "admit_s": admit_s, "calibration_s": cal_s,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 
