@@ -94,7 +94,9 @@ _P = C.c_void_p
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        # a test may point the wrapper at a deliberately broken build of the
+        # oracle (tests/test_oracle_mutations.py) to show the pins catch it
+        _lib = C.CDLL(os.environ.get("LEIDEN_ORACLE_LIB") or build())
         L = _lib
         i64, i32, d = C.c_int64, C.c_int32, C.c_double
         L.orc_gamma_ratio.argtypes = [d, _P, _P]; L.orc_gamma_ratio.restype = C.c_int

@@ -515,3 +515,56 @@ def test_degenerate_graphs():
         else:
             assert res.membership.tolist() == list(range(n))
             assert res.q == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Hand-worked single-vertex cases of the move rule (each worked out from
+# Eq. 2 scaled by 2m^2 with gamma = 1: S = 2m (K_ic - K_id) - K_i (K_i +
+# Sigma_c - Sigma_d)), with only the vertex under test unprocessed.
+# ---------------------------------------------------------------------------
+def _path_1_0_2(row0):
+    """Edges 0-1 and 0-2; row 0 lists its neighbours in the given order."""
+    off = np.array([0, 2, 3, 4], np.int64)
+    idx = np.array(list(row0) + [0, 0], np.int32)
+    return off, idx, np.ones(4, np.int64)
+
+
+@pytest.mark.parametrize("row0", [(1, 2), (2, 1)])
+def test_equal_gains_go_to_the_smallest_community_id(row0):
+    # C = identity, 2m = 4, K = (2, 1, 1): for c = 1 and c = 2 alike
+    # S = 4 (1 - 0) - 2 (2 + 1 - 2) = 2 > 0, a tie: the reading sends vertex 0
+    # to community 1 whatever the row order
+    off, idx, w = _path_1_0_2(row0)
+    C_ = np.arange(3, dtype=np.int32)
+    K = np.array([2, 1, 1], np.int64)
+    sig = K.copy()
+    processed = np.array([0, 1, 1], np.uint8)
+    # one colour class and one iteration: only vertex 0 decides
+    li, moves = O.local_move(off, idx, w, C_, K, sig, np.ones(3, np.uint8), processed, tau=0.0, max_iters=1, S=1)
+    assert moves == 1 and C_.tolist() == [1, 1, 2]
+    assert sig.tolist() == [0, 3, 1]
+
+
+def test_zero_gain_does_not_move():
+    # C = (0, 1, 0): vertex 0 sits with 2.  Towards c = 1: K_01 = 1, K_0d = 1,
+    # Sigma_1 = 1, Sigma_d = 3, so S = 4 (1 - 1) - 2 (2 + 1 - 3) = 0: not a move
+    off, idx, w = _path_1_0_2((1, 2))
+    C_ = np.array([0, 1, 0], np.int32)
+    K = np.array([2, 1, 1], np.int64)
+    sig = np.array([3, 1, 0], np.int64)
+    processed = np.array([0, 1, 1], np.uint8)
+    li, moves = O.local_move(off, idx, w, C_, K, sig, np.ones(3, np.uint8), processed, tau=0.0, max_iters=1, S=1)
+    assert moves == 0 and C_.tolist() == [0, 1, 0]
+
+
+def test_changed_flags_name_the_shared_community():
+    # communities {0, 1} (ID 1) and {2, 3} (ID 0): a deletion inside the first
+    # and an insertion inside the second flag communities 1 and 0 -- the
+    # community IDs, not the vertices' own IDs
+    Cprev = np.array([1, 1, 0, 0], np.int32)
+    one = np.ones(1, np.int32)
+    ch = O.changed_communities(Cprev, (np.array([0], np.int32), np.array([1], np.int32), one),
+                               (np.array([3], np.int32), np.array([2], np.int32), one))
+    assert ch.tolist() == [1, 1, 0, 0]
+    ch = O.changed_communities(Cprev, (np.array([1], np.int32), np.array([0], np.int32), one), None)
+    assert ch.tolist() == [0, 1, 0, 0]
