@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--serving-budget-gb", type=float, default=120.0)
     ap.add_argument("--serving-autotune", type=int, default=0)
     ap.add_argument("--serving-seed", type=int, default=5)
+    ap.add_argument("--serving-small-n", type=int, default=1 << 16)
+    ap.add_argument("--serving-small-nnz", type=int, default=1 << 18)
+    ap.add_argument("--serving-small-workers", type=int, default=2)
     return ap.parse_args()
 
 
@@ -431,12 +434,12 @@ def run_serving(args):
     torch.cuda.set_device(0)
     import paper_2405_11658_gb300 as L
     rng = np.random.default_rng(args.serving_seed)
-    small_max_n = 1 << 17
     cfg = dict(hbm_budget=int(args.serving_budget_gb * (1 << 30)), large_slots=args.serving_slots,
                small_max_graphs=64, large_max_n=max(len(g[0]) for _, g in graphs),
-               large_max_nnz=int(max(len(g[1]) for _, g in graphs) * 1.3) + 4096, small_max_n=small_max_n,
-               small_max_nnz=1 << 22, small_batch_n=1 << 22, small_batch_nnz=1 << 26, growth=0.05,
-               autotune_trials=args.serving_autotune)
+               large_max_nnz=int(max(len(g[1]) for _, g in graphs) * 1.3) + 4096,
+               small_max_n=args.serving_small_n, small_max_nnz=args.serving_small_nnz,
+               small_batch_n=1 << 22, small_batch_nnz=1 << 25, growth=0.05,
+               autotune_trials=args.serving_autotune, small_workers=args.serving_small_workers)
     with L.Server(**cfg) as srv:
         ids, admit_rids = [], []
         t_adm = time.perf_counter()
@@ -494,7 +497,9 @@ def run_serving(args):
                                f"Poisson DF update batches of 1e-6..1e-3 |E|",
                    "graphs": [f"{kind}:{len(g[0]) - 1}:{len(g[1])}" for kind, g in graphs],
                    "arrival_rate_per_s": lam, "load": args.serving_load, "large_slots": args.serving_slots,
-                   "budget_gb": args.serving_budget_gb, "autotune_trials": args.serving_autotune},
+                   "budget_gb": args.serving_budget_gb, "autotune_trials": args.serving_autotune,
+                   "small_limits": [args.serving_small_n, args.serving_small_nnz],
+                   "small_workers": args.serving_small_workers},
         "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
         "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
         "paths": per_path, "failed": len(infos) - len(ok),

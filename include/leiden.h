@@ -288,8 +288,9 @@ int leiden_batch_device_bytes(leiden_batch *b, int64_t *out);
  * the configured dynamic mode (DF by default).  Worker threads take work as
  * soon as a graph and a worker are free, so requests that arrive while others
  * run join the next launch instead of waiting for a batch boundary:
- *   - graphs within the small limits go to one worker that runs every ready
- *     small request in one persistent launch (leiden_batch_run);
+ *   - graphs within the small limits go to `small_workers` workers, each of
+ *     which runs every ready small request in one persistent launch
+ *     (leiden_batch_run), so a new launch can start while another runs;
  *   - larger graphs go to `large_slots` workers, each with its own context and
  *     stream, so their updates overlap on the device.
  * Results are DET: each request's membership does not depend on what else
@@ -311,12 +312,15 @@ typedef struct {
   int32_t mode;              /* LEIDEN_DF (default when 0) or LEIDEN_ND */
   int32_t autotune_trials;   /* > 0: leiden_autotune each large graph at admission with this many
                               * candidate tier tables and use its table for the graph's runs */
+  int32_t small_workers;     /* workers for small graphs, each with its own persistent launch in
+                              * flight (>= 1; 0 = 2) */
+  int32_t reserved;          /* must be 0 */
   leiden_opts opts;          /* DET schedule */
 } leiden_server_config;
 
-/* Fills a default configuration (HOST): 16 GB budget, 2 large slots, 64
- * graphs per persistent launch, small graphs up to 2^17 vertices / 2^22
- * entries, 25% growth, DF, default options. */
+/* Fills a default configuration (HOST): 16 GB budget, 2 large slots, 2
+ * small-graph workers, 64 graphs per persistent launch, small graphs up to
+ * 2^16 vertices / 2^18 entries, 25% growth, DF, default options. */
 void leiden_server_config_default(leiden_server_config *cfg);
 
 /* Creates a server on the current device and starts its workers.  Errors:

@@ -136,7 +136,8 @@ class _ServerConfig(C.Structure):
     _fields_ = [("hbm_budget", C.c_int64), ("large_slots", C.c_int32), ("small_max_graphs", C.c_int32),
                 ("large_max_n", C.c_int64), ("large_max_nnz", C.c_int64), ("small_max_n", C.c_int64),
                 ("small_max_nnz", C.c_int64), ("small_batch_n", C.c_int64), ("small_batch_nnz", C.c_int64),
-                ("growth", C.c_double), ("mode", C.c_int32), ("autotune_trials", C.c_int32), ("opts", _Opts)]
+                ("growth", C.c_double), ("mode", C.c_int32), ("autotune_trials", C.c_int32),
+                ("small_workers", C.c_int32), ("reserved", C.c_int32), ("opts", _Opts)]
 
 
 class _RequestInfo(C.Structure):

@@ -322,15 +322,21 @@ __device__ __forceinline__ int64_t bucket_of(int32_t c, int64_t P) {
 }
 
 // PASS = 0: count entries per bucket.  PASS = 1: scatter them.  Work item =
-// one warp-sized window of AGG_WINDOW entries of one giant community.
+// one warp-sized window of AGG_WINDOW entries of one giant community.  The
+// community's own entries (its internal weight, usually most of a giant
+// community's rows) are not bucketed: PASS 0 sums them into selfw[k] and the
+// hashing block of the bucket that key c falls in adds them as one pair, so
+// no bucket holds the bulk of a community.
 template <int PASS, typename WT>
 __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_t *C, const int32_t *list,
                                                    int64_t nlist, const int64_t *wnoff, const int64_t *nbk,
                                                    const int64_t *bkoff, const int64_t *coff, const int64_t *hoff,
                                                    const int32_t *cv, const int64_t *pdeg, u64 *bcnt,
-                                                   const int64_t *bpos, int32_t *skeys, u64 *svals, u64 *err) {
+                                                   const int64_t *bpos, int32_t *skeys, u64 *svals, u64 *selfw,
+                                                   u64 *err) {
   const int64_t nitems = wnoff[nlist];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ u64 wscr[8][32];  // blocks of 256 threads
   const int64_t w0g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwg = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t it = w0g; it < nitems; it += nwg) {  // uniform per warp
@@ -339,7 +345,18 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
     const int64_t fw0 = hoff[c] + (it - wnoff[k]) * AGG_WINDOW;
     const int64_t fw1 = fw0 + AGG_WINDOW < hoff[c + 1] ? fw0 + AGG_WINDOW : hoff[c + 1];
     const int64_t P = nbk[k], base = bkoff[k];
-    foreach_window(g, C, cv, pdeg, coff[c], coff[c + 1], fw0, fw1, err, [&](int32_t d, u64 w, bool act) {
+    foreach_window(g, C, cv, pdeg, coff[c], coff[c + 1], fw0, fw1, err, [&](int32_t d, u64 w, bool act0) {
+      const bool self = act0 && d == c;
+      if (PASS == 0) {
+        u64 sw = self ? w : 0;
+        for (int o = 16; o; o >>= 1) sw += __shfl_xor_sync(FULL_MASK, sw, o);
+        if (lane == 0 && sw) atomicAdd(&selfw[k], sw);
+      }
+      // equal targets within the warp become one pair (hot targets would
+      // otherwise fill one bucket); both passes see the same leaders
+      u64 wsum = 0;
+      const bool act = warp_combine((unsigned long long)(uint32_t)d, act0 && !self, w, &wsum, wscr[warp]);
+      w = wsum;
       const int64_t bk = act ? base + bucket_of(d, P) : -1;
       // lanes of the same bucket share one atomic
       const unsigned am = __ballot_sync(FULL_MASK, act);
@@ -366,8 +383,8 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
 // distinct targets into the community's hole range, reset the scratch.
 __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, int64_t nlist, const int64_t *nbk,
                                                    const int64_t *bkoff, const int64_t *bpos, int32_t *skeys,
-                                                   u64 *svals, const int64_t *hoff, int32_t *hidx, int64_t *hw,
-                                                   int64_t *cdist, int64_t *Kout, u64 *err) {
+                                                   u64 *svals, const u64 *selfw, const int64_t *hoff, int32_t *hidx,
+                                                   int64_t *hw, int64_t *cdist, int64_t *Kout, u64 *err) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int H = 1 << BUCKET_LOG2H;
   u64 *vals = reinterpret_cast<u64 *>(smem);
@@ -384,6 +401,13 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, int64_t 
     const int64_t p0 = bpos[bk], p1 = bpos[bk + 1];
     for (int x = threadIdx.x; x < H; x += blockDim.x) { keys[x] = LEIDEN_EMPTY_KEY; vals[x] = 0; }
     if (threadIdx.x == 0) s_ws = 0;
+    __syncthreads();
+    // the community's internal weight joins the bucket its own key falls in
+    if (threadIdx.x == 0 && selfw[k] && bk - bkoff[k] == bucket_of(c, nbk[k])) {
+      const uint32_t sl = (uint32_t)((hash32(c) << lp) >> (32 - BUCKET_LOG2H));
+      keys[sl] = c;   // the table is empty: the home slot is free
+      vals[sl] = selfw[k];
+    }
     __syncthreads();
     for (int64_t pb = p0 + 32 * warp; pb < p1; pb += 32 * (int64_t)nwarp) {  // warp-uniform
       const int64_t pos = pb + lane;
@@ -602,18 +626,20 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       if (nb + 1 > wk.bcap) return LEIDEN_ENOMEM;
       cudaMemsetAsync(wk.bcnt, 0, (size_t)(nb + 1) * sizeof(u64), s);
       const unsigned grid = (unsigned)(wk.sms * 16);
+      u64 *selfw = reinterpret_cast<u64 *>(wk.off2tmp + 4 * (nl + 1));   // [nl] internal weight
+      cudaMemsetAsync(selfw, 0, (size_t)nl * sizeof(u64), s);
       LK_COUNTED agg_bpass_k<0, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
-                                               wk.bcnt, nullptr, nullptr, nullptr, err);
+                                               wk.bcnt, nullptr, nullptr, nullptr, selfw, err);
       exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(wk.bcnt), wk.bpos, nb, wk.scan_tmp, s);
       cudaMemsetAsync(wk.bcnt, 0, (size_t)(nb + 1) * sizeof(u64), s);
       // the bucket ranges tile [0, sum of the listed total degrees) of the
       // scratch arrays, which are empty on entry and left empty
       LK_COUNTED agg_bpass_k<1, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
-                                               wk.bcnt, wk.bpos, wk.gkeys, wk.gvals, err);
+                                               wk.bcnt, wk.bpos, wk.gkeys, wk.gvals, selfw, err);
       const size_t smem = (size_t)(1u << BUCKET_LOG2H) * 12;
       ensure_smem((const void *)agg_bhash_k, smem);
       LK_COUNTED agg_bhash_k<<<(unsigned)(wk.sms * 2), 512, smem, s>>>(list, nl, nbk, bkoff, wk.bpos, wk.gkeys, wk.gvals,
-                                                            wk.hoff, wk.hidx, wk.hw, wk.cdist, Kout, err);
+                                                            selfw, wk.hoff, wk.hidx, wk.hw, wk.cdist, Kout, err);
     }
   }
   exclusive_scan<int64_t>(wk.cdist, off2, nc, wk.scan_tmp, s);

@@ -156,59 +156,86 @@ __global__ void decide_group(MoveArgs<WT> a) {
       e0 = a.g.off[i];
       e1 = a.g.off[i + 1];
       while (lh < LOG2H && ((int64_t)1 << lh) < 2 * (e1 - e0)) lh++;
-      for (int s = gl; s < (1 << lh); s += G) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     }
-    __syncwarp();
-    const int32_t cbi = (REFINE && act) ? a.CB[i] : 0;
-    if (act) d = a.C[i];
-    // warp-uniform walk over the longest row of the warp's groups, so the
-    // lanes can combine equal (group, community) keys before the atomics
+    // the longest row of the warp's groups; every loop below is warp-uniform
+    // so the lanes can combine equal (group, community) keys
     int64_t span = act ? e1 - e0 : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const int64_t y = shfl_xor_i64(span, o);
       span = y > span ? y : span;
     }
-    for (int64_t xb = 0; xb < span; xb += (int64_t)G * ROW_UNROLL) {
-      // ROW_UNROLL entries per lane: all loads and gathers first, then the
-      // warp-uniform combine and table updates
-      int32_t cc[ROW_UNROLL];
-      u64 wv[ROW_UNROLL];
-#pragma unroll
-      for (int u = 0; u < ROW_UNROLL; u++) {
-        const int64_t e = e0 + xb + (int64_t)u * G + gl;
-        const bool in = act && e < e1;
-        const int32_t j = in ? a.g.idx[e] : -1;
-        wv[u] = in ? (u64)(int64_t)a.g.w[e] : 0;
-        bool ok = in && j != i;                         // self = false
-        if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
-        cc[u] = ok ? j : -1;
-      }
-#pragma unroll
-      for (int u = 0; u < ROW_UNROLL; u++) {
-        const int32_t j = cc[u];
-        bool ok = j >= 0;
-        if (REFINE && ok && a.CB[j] != cbi) ok = false;  // scanBounded
-        cc[u] = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
-      }
-#pragma unroll
-      for (int u = 0; u < ROW_UNROLL; u++) {
-        u64 sum = 0;
-        const unsigned long long key = ((unsigned long long)(uint32_t)gw << 32) | (uint32_t)cc[u];
-        if (warp_combine(key, cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum, wscr))
-          table_add(keys, vals, lh, cc[u], sum, &a.ctr[CTR_ERROR]);
-      }
-    }
-    if (act && gl == 0) { scanned += e1 - e0; nvert++; }
+    // rows of at most G entries: one entry per lane, and the combine alone
+    // yields every distinct community with its summed weight -- no table
+    const bool one_step = span <= G;
+    if (act && !one_step)
+      for (int s = gl; s < (1 << lh); s += G) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     __syncwarp();
+    const int32_t cbi = (REFINE && act) ? a.CB[i] : 0;
+    if (act) d = a.C[i];
     ST bsc = 0;
     int32_t bc = INT32_MAX;
     int64_t kid = 0;
-    if (act) {
-      const ST A = (ST)a.A;
-      const ST B = (ST)a.p * (ST)a.K[i];
-      scan_slots<ST>(keys, vals, 1 << lh, gl, G, d, A, B, a.Sig, bsc, bc, kid, ncand);
+    if (one_step) {
+      const int64_t e = e0 + gl;
+      const bool in = act && e < e1;
+      const int32_t j = in ? a.g.idx[e] : -1;
+      const u64 wv = in ? (u64)(int64_t)a.g.w[e] : 0;
+      bool ok = in && j != i;                            // self = false
+      if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
+      if (REFINE && ok && a.CB[j] != cbi) ok = false;    // scanBounded
+      const int32_t c = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
+      u64 sum = 0;
+      const unsigned long long key = ((unsigned long long)(uint32_t)gw << 32) | (uint32_t)c;
+      if (warp_combine(key, ok, wv, &sum, wscr)) {
+        ncand++;
+        if (c == d) {
+          kid = (int64_t)sum;
+        } else {
+          const ST sc = (ST)a.A * (ST)(int64_t)sum - (ST)a.p * (ST)a.K[i] * (ST)a.Sig[c];
+          bsc = sc;
+          bc = c;
+        }
+      }
+    } else {
+      for (int64_t xb = 0; xb < span; xb += (int64_t)G * ROW_UNROLL) {
+        // ROW_UNROLL entries per lane: all loads and gathers first, then the
+        // warp-uniform combine and table updates
+        int32_t cc[ROW_UNROLL];
+        u64 wv[ROW_UNROLL];
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; u++) {
+          const int64_t e = e0 + xb + (int64_t)u * G + gl;
+          const bool in = act && e < e1;
+          const int32_t j = in ? a.g.idx[e] : -1;
+          wv[u] = in ? (u64)(int64_t)a.g.w[e] : 0;
+          bool ok = in && j != i;                         // self = false
+          if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
+          cc[u] = ok ? j : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; u++) {
+          const int32_t j = cc[u];
+          bool ok = j >= 0;
+          if (REFINE && ok && a.CB[j] != cbi) ok = false;  // scanBounded
+          cc[u] = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
+        }
+#pragma unroll
+        for (int u = 0; u < ROW_UNROLL; u++) {
+          u64 sum = 0;
+          const unsigned long long key = ((unsigned long long)(uint32_t)gw << 32) | (uint32_t)cc[u];
+          if (warp_combine(key, cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum, wscr))
+            table_add(keys, vals, lh, cc[u], sum, &a.ctr[CTR_ERROR]);
+        }
+      }
+      __syncwarp();
+      if (act) {
+        const ST A = (ST)a.A;
+        const ST B = (ST)a.p * (ST)a.K[i];
+        scan_slots<ST>(keys, vals, 1 << lh, gl, G, d, A, B, a.Sig, bsc, bc, kid, ncand);
+      }
     }
+    if (act && gl == 0) { scanned += e1 - e0; nvert++; }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
       const ST osc = shfl_xor_any<ST>(bsc, o);

@@ -2,8 +2,9 @@
 // against a device-memory budget, per-graph FIFO queues of update batches,
 // and worker threads that pick work as soon as a graph and a worker are free
 // (continuous batching):
-//   * one small-graph worker drains every ready request of a small graph into
-//     one persistent launch (leiden_batch_run), after building each G^t;
+//   * `small_workers` small-graph workers, each draining every ready request
+//     of a small graph into one persistent launch (leiden_batch_run) after
+//     building each G^t, so one launch can start while another runs;
 //   * `large_slots` workers, each with its own leiden_ctx and stream, run the
 //     updates of large graphs concurrently on the device.
 // Host code only; every step on the device is a library call.
@@ -83,10 +84,13 @@ struct leiden_server {
   std::vector<leiden_ctx *> large_ctx;
   std::vector<cudaStream_t> large_st;
   std::vector<Staging> large_stage;
-  leiden_ctx *small_ctx = nullptr;
-  leiden_batch *small_batch = nullptr;
-  cudaStream_t small_st = nullptr;
-  Staging small_stage;
+  struct Small {
+    leiden_ctx *ctx = nullptr;
+    leiden_batch *batch = nullptr;
+    cudaStream_t st = nullptr;
+    Staging stage;
+  };
+  std::vector<Small> small;
 };
 
 namespace {
@@ -203,11 +207,12 @@ void run_large(leiden_server *s, int k, Resident *g, Request *r) {
 }
 
 // The ready requests of small graphs, in one persistent launch.
-void run_small(leiden_server *s, std::vector<std::pair<Resident *, Request *>> &work) {
-  cudaStream_t st = s->small_st;
+void run_small(leiden_server *s, int w, std::vector<std::pair<Resident *, Request *>> &work) {
+  leiden_server::Small &sw = s->small[w];
+  cudaStream_t st = sw.st;
   int64_t words = 0;
   for (auto &x : work) words += batch_words(*x.second);
-  int rc0 = grow(s, s->small_stage, words);
+  int rc0 = grow(s, sw.stage, words);
   std::vector<leiden_batch_item> items;
   std::vector<int> slot_of(work.size(), -1);
   std::vector<int64_t> nnz2(work.size(), 0);
@@ -226,11 +231,11 @@ void run_small(leiden_server *s, std::vector<std::pair<Resident *, Request *>> &
       nnz2[k] = g->nnz;
     } else {
       leiden_edges del{}, ins{};
-      upload_batch(*r, s->small_stage.buf + at, st, &del, &ins);
+      upload_batch(*r, sw.stage.buf + at, st, &del, &ins);
       at += batch_words(*r);
       const int nx = 1 - g->csr;
       leiden_csr cur = csr_of(*g, g->csr, g->nnz);
-      const int rc = leiden_apply_batch(s->small_ctx, &cur, &del, &ins, g->off[nx], g->idx[nx], g->w[nx], g->cap,
+      const int rc = leiden_apply_batch(sw.ctx, &cur, &del, &ins, g->off[nx], g->idx[nx], g->w[nx], g->cap,
                                         &nnz2[k]);
       if (rc) { r->info.status = rc; continue; }
       it.g = csr_of(*g, nx, nnz2[k]);
@@ -244,7 +249,7 @@ void run_small(leiden_server *s, std::vector<std::pair<Resident *, Request *>> &
   }
   std::vector<leiden_batch_result> res(items.size());
   int rc = LEIDEN_OK;
-  if (!items.empty()) rc = leiden_batch_run(s->small_batch, (int32_t)items.size(), items.data(), &s->cfg.opts,
+  if (!items.empty()) rc = leiden_batch_run(sw.batch, (int32_t)items.size(), items.data(), &s->cfg.opts,
                                             res.data());
   for (size_t k = 0; k < work.size(); k++) {
     Resident *g = work[k].first;
@@ -307,7 +312,7 @@ void large_worker(leiden_server *s, int k) {
   }
 }
 
-void small_worker(leiden_server *s) {
+void small_worker(leiden_server *s, int wk) {
   cudaSetDevice(s->device);
   for (;;) {
     std::vector<std::pair<Resident *, Request *>> work;
@@ -334,7 +339,7 @@ void small_worker(leiden_server *s) {
       }
       if (work.empty()) return;  // stopping with nothing to do
     }
-    run_small(s, work);
+    run_small(s, wk, work);
   }
 }
 
@@ -353,10 +358,11 @@ extern "C" void leiden_server_config_default(leiden_server_config *c) {
   c->small_max_graphs = 64;
   c->large_max_n = (int64_t)1 << 24;
   c->large_max_nnz = (int64_t)1 << 28;
-  c->small_max_n = (int64_t)1 << 17;
-  c->small_max_nnz = (int64_t)1 << 22;
-  c->small_batch_n = (int64_t)1 << 22;
-  c->small_batch_nnz = (int64_t)1 << 26;
+  c->small_max_n = (int64_t)1 << 16;
+  c->small_max_nnz = (int64_t)1 << 18;
+  c->small_batch_n = (int64_t)1 << 21;
+  c->small_batch_nnz = (int64_t)1 << 24;
+  c->small_workers = 2;
   c->growth = 0.25;
   c->mode = LEIDEN_DF;
   leiden_opts_default(&c->opts);
@@ -367,6 +373,8 @@ extern "C" int leiden_server_create(leiden_server **out, const leiden_server_con
   leiden_server_config c = *cfg;
   if (c.mode == 0) c.mode = LEIDEN_DF;
   if (c.mode != LEIDEN_DF && c.mode != LEIDEN_ND) return LEIDEN_EINVAL;
+  if (c.small_workers == 0) c.small_workers = 2;
+  if (c.small_workers < 1 || c.small_workers > 8 || c.reserved) return LEIDEN_EINVAL;
   if (c.large_slots < 1 || c.large_slots > 16 || c.small_max_graphs < 1 || c.autotune_trials < 0) return LEIDEN_EINVAL;
   if (c.hbm_budget <= 0 || c.large_max_n < 1 || c.large_max_nnz < 1 || c.small_max_n < 1 || c.small_max_nnz < 1)
     return LEIDEN_EINVAL;
@@ -389,33 +397,35 @@ extern "C" int leiden_server_create(leiden_server **out, const leiden_server_con
     leiden_ctx_device_bytes(ctx, &b);
     s->workspace_bytes += b;
   }
-  if (!rc && cudaStreamCreateWithFlags(&s->small_st, cudaStreamNonBlocking) != cudaSuccess) rc = LEIDEN_ECUDA;
-  if (!rc) rc = leiden_ctx_create(&s->small_ctx, s->small_st, c.small_max_n, c.small_max_nnz);
-  if (!rc) {
+  s->small.resize(c.small_workers);
+  for (int k = 0; k < c.small_workers && !rc; k++) {
+    leiden_server::Small &sw = s->small[k];
+    if (cudaStreamCreateWithFlags(&sw.st, cudaStreamNonBlocking) != cudaSuccess) { rc = LEIDEN_ECUDA; break; }
+    rc = leiden_ctx_create(&sw.ctx, sw.st, c.small_max_n, c.small_max_nnz);
+    if (rc) break;
     int64_t b = 0;
-    leiden_ctx_device_bytes(s->small_ctx, &b);
+    leiden_ctx_device_bytes(sw.ctx, &b);
     s->workspace_bytes += b;
-    rc = leiden_batch_create(&s->small_batch, s->small_st, c.small_max_graphs, c.small_batch_n, c.small_batch_nnz,
-                             0, 0);
-  }
-  if (!rc) {
-    int64_t b = 0;
-    leiden_batch_device_bytes(s->small_batch, &b);
+    rc = leiden_batch_create(&sw.batch, sw.st, c.small_max_graphs, c.small_batch_n, c.small_batch_nnz, 0, 0);
+    if (rc) break;
+    leiden_batch_device_bytes(sw.batch, &b);
     s->workspace_bytes += b;
   }
   if (!rc && s->workspace_bytes > c.hbm_budget) rc = LEIDEN_ENOMEM;
   if (rc) {
     for (leiden_ctx *x : s->large_ctx) leiden_ctx_destroy(x);
     for (cudaStream_t x : s->large_st) cudaStreamDestroy(x);
-    if (s->small_ctx) leiden_ctx_destroy(s->small_ctx);
-    if (s->small_batch) leiden_batch_destroy(s->small_batch);
-    if (s->small_st) cudaStreamDestroy(s->small_st);
+    for (auto &sw : s->small) {
+      if (sw.ctx) leiden_ctx_destroy(sw.ctx);
+      if (sw.batch) leiden_batch_destroy(sw.batch);
+      if (sw.st) cudaStreamDestroy(sw.st);
+    }
     delete s;
     return rc;
   }
   s->large_stage.resize(c.large_slots);
   for (int k = 0; k < c.large_slots; k++) s->threads.emplace_back(large_worker, s, k);
-  s->threads.emplace_back(small_worker, s);
+  for (int k = 0; k < c.small_workers; k++) s->threads.emplace_back(small_worker, s, k);
   *out = s;
   return LEIDEN_OK;
 }
@@ -434,10 +444,12 @@ extern "C" void leiden_server_destroy(leiden_server *s) {
   for (leiden_ctx *x : s->large_ctx) leiden_ctx_destroy(x);
   for (cudaStream_t x : s->large_st) cudaStreamDestroy(x);
   for (Staging &sg : s->large_stage) if (sg.buf) cudaFree(sg.buf);
-  if (s->small_stage.buf) cudaFree(s->small_stage.buf);
-  leiden_ctx_destroy(s->small_ctx);
-  leiden_batch_destroy(s->small_batch);
-  cudaStreamDestroy(s->small_st);
+  for (auto &sw : s->small) {
+    if (sw.stage.buf) cudaFree(sw.stage.buf);
+    leiden_ctx_destroy(sw.ctx);
+    leiden_batch_destroy(sw.batch);
+    cudaStreamDestroy(sw.st);
+  }
   delete s;
 }
 
