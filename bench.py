@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default="rmat", choices=["rmat", "serving"])
+    ap.add_argument("--profile-static", action="store_true",
+                    help="run one Static Leiden on the workload graph and print its statistics (for profilers)")
     ap.add_argument("--serving-graphs", type=int, default=64)
     ap.add_argument("--serving-max-n", type=float, default=1e7)
     ap.add_argument("--serving-per-graph", type=int, default=10)
@@ -511,8 +513,36 @@ def run_serving(args):
     return 0
 
 
+def run_profile_static(args):
+    """One Static Leiden (DET) on the benchmark graph with the decide kernels
+    timed; prints the run's statistics as one JSON line.  A profiler run over
+    this command sees exactly one run's launches (local-moving inside the
+    NVTX range "local_move", refinement in "refine", aggregation in
+    "aggregate")."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2405_11658_gb300 as L
+    g, _ = make_inputs(args.scale, GRAPH_SEED, 0)
+    G = L.Graph.from_numpy(*g)
+    with L.Context(max_n=len(g[0]) - 1, max_nnz=len(g[1]) + 16) as ctx:
+        ctx.set_timing(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, q = ctx.static(G, L.Opts(sched=L.DET if args.sched == "det" else L.ASYNC))
+        torch.cuda.synchronize()
+        ms = 1000 * (time.perf_counter() - t0)
+        st = ctx.stats()
+    keep = ("passes", "iters", "nv", "nnz", "moves", "refine_moves", "move_kernel_ms", "move_kernel_launches",
+            "move_scanned_entries", "move_scanned_vertices", "move_bytes", "t_move_ms", "t_refine_ms", "t_agg_ms")
+    print(json.dumps({"workload": f"rmat-s{args.scale}-ef{EDGE_FACTOR} static leiden", "ms": ms, "q": q,
+                      **{k: st[k] for k in keep}}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_static:
+        return run_profile_static(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(512) agg_block_k(GraphView<WT> g, const int32_
 // ---------------------------------------------------------------------------
 static constexpr int BUCKET_KEYS = 2048;      // expected distinct targets per bucket
 static constexpr int64_t AGG_WINDOW = 512;    // flat entries per warp work item
-static constexpr int BUCKET_LOG2H = 13;       // 8192-slot table (96 KB): 4x headroom
+static constexpr uint32_t BUCKET_SLOTS = 6144;  // shared table of a bucket: 3x headroom
 
 __global__ void agg_bsize_k(const int32_t *list, int64_t nlist, const int64_t *hoff, int64_t nc, int64_t *nbk,
                             int64_t *nwin) {
@@ -380,33 +380,45 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
 }
 
 // One block per bucket: hash the bucket's pairs in shared memory, emit the
-// distinct targets into the community's hole range, reset the scratch.
+// distinct targets into the community's hole range, reset the scratch.  The
+// table is cleared once per block; every bucket lists the slots it occupies
+// and resets exactly those while emitting them, so a bucket costs work in
+// proportion to its pairs, not to the table size.
 __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, int64_t nlist, const int64_t *nbk,
                                                    const int64_t *bkoff, const int64_t *bpos, int32_t *skeys,
                                                    u64 *svals, const u64 *selfw, const int64_t *hoff, int32_t *hidx,
                                                    int64_t *hw, int64_t *cdist, int64_t *Kout, u64 *err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int H = 1 << BUCKET_LOG2H;
+  constexpr uint32_t H = BUCKET_SLOTS;
   u64 *vals = reinterpret_cast<u64 *>(smem);
   int32_t *keys = reinterpret_cast<int32_t *>(vals + H);
+  uint16_t *used = reinterpret_cast<uint16_t *>(keys + H);
   __shared__ u64 wscratch[16][32];
   __shared__ int64_t s_ws;
+  __shared__ unsigned s_nused;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const int64_t nb = bkoff[nlist];
+  for (uint32_t x = threadIdx.x; x < H; x += blockDim.x) { keys[x] = LEIDEN_EMPTY_KEY; vals[x] = 0; }
+  if (threadIdx.x == 0) s_nused = 0;
   for (int64_t bk = blockIdx.x; bk < nb; bk += gridDim.x) {
     const int64_t k = find_k(bkoff, nlist, bk);
     const int32_t c = list[k];
     int lp = 0;
     while (((int64_t)1 << lp) < nbk[k]) lp++;
     const int64_t p0 = bpos[bk], p1 = bpos[bk + 1];
-    for (int x = threadIdx.x; x < H; x += blockDim.x) { keys[x] = LEIDEN_EMPTY_KEY; vals[x] = 0; }
     if (threadIdx.x == 0) s_ws = 0;
     __syncthreads();
+    // the bucket's keys share their top lp hash bits: index by the next ones
+    // (scaled to the table size)
+    auto home = [&](int32_t key) -> uint32_t {
+      return (uint32_t)(((u64)(uint32_t)(hash32(key) << lp) * H) >> 32);
+    };
     // the community's internal weight joins the bucket its own key falls in
     if (threadIdx.x == 0 && selfw[k] && bk - bkoff[k] == bucket_of(c, nbk[k])) {
-      const uint32_t sl = (uint32_t)((hash32(c) << lp) >> (32 - BUCKET_LOG2H));
-      keys[sl] = c;   // the table is empty: the home slot is free
+      const uint32_t sl = home(c);   // the table is empty: the home slot is free
+      keys[sl] = c;
       vals[sl] = selfw[k];
+      used[s_nused++] = (uint16_t)sl;
     }
     __syncthreads();
     for (int64_t pb = p0 + 32 * warp; pb < p1; pb += 32 * (int64_t)nwarp) {  // warp-uniform
@@ -421,31 +433,38 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, int64_t 
       }
       u64 sum = 0;
       if (warp_combine((unsigned long long)(uint32_t)d, d != LEIDEN_EMPTY_KEY, w, &sum, wscratch[warp])) {
-        // the bucket's keys share their top lp hash bits: index by the next ones
-        const uint32_t mask = H - 1;
-        uint32_t sl = (uint32_t)((hash32(d) << lp) >> (32 - BUCKET_LOG2H));
+        uint32_t sl = home(d);
         bool done = false;
-        for (uint32_t probe = 0; probe < (uint32_t)H && !done; probe++) {
+        for (uint32_t probe = 0; probe < H && !done; probe++) {
           const int32_t kk = *(volatile int32_t *)&keys[sl];
           if (kk == d) { atomicAdd(&vals[sl], sum); done = true; }
           else if (kk == LEIDEN_EMPTY_KEY) {
             const int32_t old = atomicCAS(&keys[sl], LEIDEN_EMPTY_KEY, d);
+            if (old == LEIDEN_EMPTY_KEY) used[atomicAdd(&s_nused, 1u)] = (uint16_t)sl;
             if (old == LEIDEN_EMPTY_KEY || old == d) { atomicAdd(&vals[sl], sum); done = true; }
           }
-          sl = (sl + 1) & mask;
+          sl = sl + 1 == H ? 0 : sl + 1;
         }
         if (!done) atomicOr(err, 16ull);
       }
     }
     __syncthreads();
+    const unsigned nused = s_nused;
     int64_t ws = 0;
-    for (int x0 = 32 * warp; x0 < H; x0 += 32 * nwarp) {  // warp-uniform
-      const int x = x0 + lane;
-      const int32_t key = keys[x];
-      const bool occ = key != LEIDEN_EMPTY_KEY;
+    for (unsigned u0 = 32 * warp; u0 < nused; u0 += 32 * nwarp) {  // warp-uniform
+      const unsigned u = u0 + lane;
+      const bool occ = u < nused;
+      int32_t key = LEIDEN_EMPTY_KEY;
+      int64_t v = 0;
+      if (occ) {
+        const uint32_t sl = used[u];
+        key = keys[sl];
+        v = (int64_t)vals[sl];
+        keys[sl] = LEIDEN_EMPTY_KEY;   // reset on read: clean for the next bucket
+        vals[sl] = 0;
+      }
       const u64 slot = warp_reserve((u64 *)&cdist[c], occ);
       if (occ) {
-        const int64_t v = (int64_t)vals[x];
         hidx[hoff[c] + (int64_t)slot] = key;
         hw[hoff[c] + (int64_t)slot] = v;
         ws += v;
@@ -454,7 +473,10 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, int64_t 
     for (int o = 16; o; o >>= 1) ws += shfl_xor_i64(ws, o);
     if (lane == 0 && ws) atomicAdd((u64 *)&s_ws, (u64)ws);
     __syncthreads();
-    if (threadIdx.x == 0 && s_ws) atomicAdd((u64 *)&Kout[c], (u64)s_ws);
+    if (threadIdx.x == 0) {
+      if (s_ws) atomicAdd((u64 *)&Kout[c], (u64)s_ws);
+      s_nused = 0;
+    }
     __syncthreads();
   }
 }
@@ -636,7 +658,7 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       // scratch arrays, which are empty on entry and left empty
       LK_COUNTED agg_bpass_k<1, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
                                                wk.bcnt, wk.bpos, wk.gkeys, wk.gvals, selfw, err);
-      const size_t smem = (size_t)(1u << BUCKET_LOG2H) * 12;
+      const size_t smem = (size_t)BUCKET_SLOTS * (12 + 2);
       ensure_smem((const void *)agg_bhash_k, smem);
       LK_COUNTED agg_bhash_k<<<(unsigned)(wk.sms * 2), 512, smem, s>>>(list, nl, nbk, bkoff, wk.bpos, wk.gkeys, wk.gvals,
                                                             selfw, wk.hoff, wk.hidx, wk.hw, wk.cdist, Kout, err);

@@ -13,11 +13,22 @@
 #include <chrono>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "internal.h"
 #include "leiden.h"
 
 using namespace lk;
+
+namespace {
+// NVTX range around a phase ("local_move", "refine", "aggregate"), so a
+// profiler can select a phase's kernels; free when no tool is attached.
+struct Phase {
+  explicit Phase(const char *name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace lk {
 static std::atomic<uint64_t> g_kernel_launches{0};
@@ -449,7 +460,11 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
     if (((int64_t)1 << lh) > c->gcap) return LEIDEN_ENOMEM;
   }
   int64_t moves = 0, rmoves = 0;
-  const int li = local_move<WT, ST>(r, g, b, lp == 0, tau, &moves);
+  int li;
+  {
+    Phase ph("local_move");
+    li = local_move<WT, ST>(r, g, b, lp == 0, tau, &moves);
+  }
   if (li < 0) return li;
   if (lp == 0) c->stats.changed0 = count_flags(c, c->ch, nv);
   if (rec) c->stats.t_move_ms[lp] = ms_since(t_start);
@@ -460,7 +475,10 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
   std::swap(c->ch, c->ch2);
   if (nv > 0) cudaMemcpyAsync(c->CB, c->Cp, (size_t)nv * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st);
   launch_break(nv, c->Cp, c->Kp, c->Sp, c->ch, c->st);
-  rc = refine<WT, ST>(r, g, b, &rmoves);
+  {
+    Phase ph("refine");
+    rc = refine<WT, ST>(r, g, b, &rmoves);
+  }
   if (rc) return rc;
   if (rec) c->stats.t_refine_ms[lp] = ms_since(t_ref);
   const auto t_agg = std::chrono::steady_clock::now();
@@ -487,7 +505,10 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
   }
   launch_lookup(r.N, c->Ctop, c->Cp, c->st);
   int64_t nnz2 = 0;
-  rc = aggregate<WT>(g, c->Cp, nc, c->goff[dst], c->gidx[dst], c->gw[dst], &nnz2, agg_work(c), c->st);
+  {
+    Phase ph("aggregate");
+    rc = aggregate<WT>(g, c->Cp, nc, c->goff[dst], c->gidx[dst], c->gw[dst], &nnz2, agg_work(c), c->st);
+  }
   if (rc) return rc;
   cudaMemcpyAsync(&c->h_ctr[CTR_ERROR], &c->ctr[CTR_ERROR], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
   rc = sync(c);

@@ -293,10 +293,30 @@ __global__ void decide_group(MoveArgs<WT> a) {
 }
 
 // ---------------------------------------------------------------------------
-// Block tiers: one block per vertex; table in shared memory (GLOBAL = false)
-// or in this block's slice of global scratch (GLOBAL = true, hub rows).
+// Block tiers: one block per vertex, table in shared memory.  The table is
+// cleared once per block; each vertex lists the slots it occupies and the
+// scan resets exactly those while reading them, so a vertex costs work in
+// proportion to its row, not to the table size.
 // ---------------------------------------------------------------------------
-template <bool GLOBAL, bool REFINE, bool ASYNC, typename WT, typename ST>
+// Insert into a listed table: a newly occupied slot is appended to `used`.
+__device__ __forceinline__ void table_add_listed(int32_t *keys, u64 *vals, int log2H, int32_t c, u64 w,
+                                                 uint16_t *used, unsigned *nused, u64 *err) {
+  const uint32_t mask = (1u << log2H) - 1u;
+  uint32_t s = hash32(c) >> (32 - log2H);
+  for (uint32_t probe = 0; probe <= mask; probe++) {
+    int32_t k = *(volatile int32_t *)&keys[s];
+    if (k == c) { atomicAdd(&vals[s], w); return; }
+    if (k == LEIDEN_EMPTY_KEY) {
+      int32_t old = atomicCAS(&keys[s], LEIDEN_EMPTY_KEY, c);
+      if (old == LEIDEN_EMPTY_KEY) used[atomicAdd(nused, 1u)] = (uint16_t)s;
+      if (old == LEIDEN_EMPTY_KEY || old == c) { atomicAdd(&vals[s], w); return; }
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(err, 16ull);
+}
+
+template <bool REFINE, bool ASYNC, typename WT, typename ST>
 __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int32_t s_i, s_d, s_act;
@@ -305,20 +325,17 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
   __shared__ int32_t r_c[32];
   __shared__ int64_t r_kid[32];
   __shared__ int32_t s_mv;
+  __shared__ unsigned s_nused;
   __shared__ u64 wscratch[32][32];
   const int Hmax = 1 << log2H;
-  u64 *vals;
-  int32_t *keys;
-  if (GLOBAL) {
-    vals = a.gvals + (size_t)blockIdx.x * Hmax;
-    keys = a.gkeys + (size_t)blockIdx.x * Hmax;
-  } else {
-    vals = reinterpret_cast<u64 *>(smem);
-    keys = reinterpret_cast<int32_t *>(vals + Hmax);
-  }
+  u64 *vals = reinterpret_cast<u64 *>(smem);
+  int32_t *keys = reinterpret_cast<int32_t *>(vals + Hmax);
+  uint16_t *used = reinterpret_cast<uint16_t *>(keys + Hmax);   // Hmax / 2 entries
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   int64_t scanned = 0, nvert = 0, ncand = 0, nmoves = 0;
   i128 accS = 0;
+  for (int s = threadIdx.x; s < Hmax; s += blockDim.x) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
+  if (threadIdx.x == 0) s_nused = 0;
   for (int64_t li = blockIdx.x; li < a.list_n; li += gridDim.x) {
     if (threadIdx.x == 0) {
       const int32_t i = a.list[li];
@@ -334,9 +351,6 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
     // table sized for this row: at least 2 * degree slots, at most the tier's
     int lh = 1;
     while (lh < log2H && ((int64_t)1 << lh) < 2 * (e1 - e0)) lh++;
-    const int H = 1 << lh;
-    for (int s = threadIdx.x; s < H; s += blockDim.x) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
-    __syncthreads();
     const int32_t cbi = REFINE ? a.CB[i] : 0;
     // each warp walks 32-entry chunks (warp-uniform), combining equal
     // communities across its lanes before the atomics
@@ -365,17 +379,28 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
         u64 sum = 0;
         if (warp_combine((unsigned long long)(uint32_t)cc[u], cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum,
                          wscratch[warp]))
-          table_add(keys, vals, lh, cc[u], sum, &a.ctr[CTR_ERROR]);
+          table_add_listed(keys, vals, lh, cc[u], sum, used, &s_nused, &a.ctr[CTR_ERROR]);
       }
     }
     if (threadIdx.x == 0) { scanned += e1 - e0; nvert++; }
     __syncthreads();
+    const unsigned nused = s_nused;
     const ST A = (ST)a.A;
     const ST B = (ST)a.p * (ST)a.K[i];
     ST bsc = 0;
     int32_t bc = INT32_MAX;
     int64_t kid = 0;
-    scan_slots<ST>(keys, vals, H, threadIdx.x, blockDim.x, d, A, B, a.Sig, bsc, bc, kid, ncand);
+    for (unsigned u = threadIdx.x; u < nused; u += blockDim.x) {
+      const uint32_t sl = used[u];
+      const int32_t c = keys[sl];
+      const int64_t v = (int64_t)vals[sl];
+      keys[sl] = LEIDEN_EMPTY_KEY;   // reset on read: clean for the next vertex
+      vals[sl] = 0;
+      ncand++;
+      if (c == d) { kid = v; continue; }
+      const ST sc = A * (ST)v - B * (ST)a.Sig[c];
+      if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const ST osc = shfl_xor_any<ST>(bsc, o);
@@ -386,6 +411,7 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
     if (lane == 0) { r_sc[warp] = bsc; r_c[warp] = bc; r_kid[warp] = kid; }
     __syncthreads();
     if (threadIdx.x == 0) {
+      s_nused = 0;
       for (int k = 1; k < nwarp; k++) {
         kid += r_kid[k];
         if (better(r_sc[k], r_c[k], bsc, bc)) { bsc = r_sc[k]; bc = r_c[k]; }
@@ -536,11 +562,12 @@ void launch_decide(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s
   }
   if (t.kind != TIER_BLOCK) return;  // hub rows go through launch_hubs
   const int log2H = t.log2H;
-  const size_t smem = (size_t)(1u << log2H) * (sizeof(u64) + sizeof(int32_t));
+  // table (value, key) plus the list of used slots (at most half the table)
+  const size_t smem = (size_t)(1u << log2H) * (sizeof(u64) + sizeof(int32_t)) + (size_t)(1u << log2H);
   int64_t blocks = a.list_n;
   const int64_t cap = (int64_t)sms * 8;
   if (blocks > cap) blocks = cap;
-  auto k = decide_block<false, REFINE, ASYNC, WT, ST>;
+  auto k = decide_block<REFINE, ASYNC, WT, ST>;
   ensure_smem((const void *)k, smem);
   LK_COUNTED k<<<(unsigned)blocks, t.threads, smem, s>>>(a, log2H);
 }

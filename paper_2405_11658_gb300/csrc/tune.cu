@@ -93,7 +93,8 @@ extern "C" int leiden_tiers_validate(const leiden_tier_table *t) {
     } else if (s.kind == LEIDEN_TIER_BLOCK) {
       if (s.lanes != 0 || s.log2_slots < 6 || s.log2_slots > 14) return LEIDEN_EINVAL;
       if (s.threads < 64 || s.threads > 1024) return LEIDEN_EINVAL;
-      if (((int64_t)1 << s.log2_slots) * kSlotBytes + kBlockStaticSmem > kSmemPerBlock) return LEIDEN_EINVAL;
+      // 12 bytes per slot plus a 2-byte used-slot list of half the table
+      if (((int64_t)1 << s.log2_slots) * (kSlotBytes + 1) + kBlockStaticSmem > kSmemPerBlock) return LEIDEN_EINVAL;
     } else {
       return LEIDEN_EINVAL;
     }
