@@ -84,6 +84,36 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# The decide kernels' sources: a DRAM-traffic figure measured by ncu (stored
+# under profiles/) stays valid only while these files are unchanged.
+DECIDE_SOURCES = ("paper_2405_11658_gb300/csrc/move.cu", "paper_2405_11658_gb300/csrc/hub.cu",
+                  "paper_2405_11658_gb300/csrc/internal.h", "paper_2405_11658_gb300/csrc/common.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "decide_traffic_rmat22.json")
+
+
+def decide_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in DECIDE_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(scale):
+    """DRAM bytes per local-moving sub-sweep of the decide kernels, from the
+    ncu capture recorded in profiles/ -- or None when there is none for this
+    workload or the kernels changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("scale") != scale or d.get("source_sha256") != decide_sources_sha():
+        return None
+    return float(d["dram_bytes_per_launch"])
+
+
 class Clocks:
     """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
 
@@ -343,7 +373,7 @@ def run_ours(args):
             "static_passes": last.get("passes"), "static_iters": last.get("iters"),
             "df": df,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None, "traffic": measured_traffic(args.scale),
                          "kernel": "local-move decide (all degree tiers)", "peak_kind": peak_kind,
                          "bytes_per_launch": mv_bytes / max(1, mv_launches),
                          "ms_per_launch": mv_ms / max(1, mv_launches), "launches": mv_launches},

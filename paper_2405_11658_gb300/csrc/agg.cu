@@ -384,10 +384,19 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
 // table is cleared once per block; every bucket lists the slots it occupies
 // and resets exactly those while emitting them, so a bucket costs work in
 // proportion to its pairs, not to the table size.
-__global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, int64_t nlist, const int64_t *nbk,
+// Owner (index into the giant list) of every bucket, so a hashing block finds
+// its bucket's community with one load instead of a binary search.
+__global__ void agg_bown_k(const int64_t *bkoff, int64_t nlist, int32_t *bown) {
+  GSTRIDE(k, nlist) {
+    for (int64_t b = bkoff[k]; b < bkoff[k + 1]; b++) bown[b] = (int32_t)k;
+  }
+}
+
+__global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, const int32_t *bown, const int64_t *nbk,
                                                    const int64_t *bkoff, const int64_t *bpos, int32_t *skeys,
                                                    u64 *svals, const u64 *selfw, const int64_t *hoff, int32_t *hidx,
-                                                   int64_t *hw, int64_t *cdist, int64_t *Kout, u64 *err) {
+                                                   int64_t *hw, int64_t *cdist, int64_t *Kout, int64_t nb,
+                                                   u64 *err) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr uint32_t H = BUCKET_SLOTS;
   u64 *vals = reinterpret_cast<u64 *>(smem);
@@ -397,11 +406,10 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, int64_t 
   __shared__ int64_t s_ws;
   __shared__ unsigned s_nused;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  const int64_t nb = bkoff[nlist];
   for (uint32_t x = threadIdx.x; x < H; x += blockDim.x) { keys[x] = LEIDEN_EMPTY_KEY; vals[x] = 0; }
   if (threadIdx.x == 0) s_nused = 0;
   for (int64_t bk = blockIdx.x; bk < nb; bk += gridDim.x) {
-    const int64_t k = find_k(bkoff, nlist, bk);
+    const int64_t k = bown[bk];
     const int32_t c = list[k];
     int lp = 0;
     while (((int64_t)1 << lp) < nbk[k]) lp++;
@@ -660,8 +668,12 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
                                                wk.bcnt, wk.bpos, wk.gkeys, wk.gvals, selfw, err);
       const size_t smem = (size_t)BUCKET_SLOTS * (12 + 2);
       ensure_smem((const void *)agg_bhash_k, smem);
-      LK_COUNTED agg_bhash_k<<<(unsigned)(wk.sms * 2), 512, smem, s>>>(list, nl, nbk, bkoff, wk.bpos, wk.gkeys, wk.gvals,
-                                                            selfw, wk.hoff, wk.hidx, wk.hw, wk.cdist, Kout, err);
+      // the bucket counters are free after the scatter: they hold the owners
+      int32_t *bown = reinterpret_cast<int32_t *>(wk.bcnt);
+      LK_COUNTED agg_bown_k<<<gridn(nl, 256), 256, 0, s>>>(bkoff, nl, bown);
+      LK_COUNTED agg_bhash_k<<<(unsigned)(wk.sms * 2), 512, smem, s>>>(list, bown, nbk, bkoff, wk.bpos, wk.gkeys,
+                                                            wk.gvals, selfw, wk.hoff, wk.hidx, wk.hw, wk.cdist, Kout,
+                                                            nb, err);
     }
   }
   exclusive_scan<int64_t>(wk.cdist, off2, nc, wk.scan_tmp, s);

@@ -20,6 +20,16 @@
 
 namespace lk {
 
+// Value type of the shared-memory tables.  The 64-bit score path is taken only
+// when 4 (2m)^2 max(p, q) < 2^62, so 2m < 2^31 and every summed K_{i->c}
+// (at most K_i <= 2m) fits 32 bits: those tables hold 8-byte slots instead
+// of 12, and more warps fit on an SM.
+template <typename ST> struct TableVal { typedef u64 type; };
+template <> struct TableVal<int64_t> { typedef uint32_t type; };
+
+__device__ __forceinline__ void add_val(u64 *p, u64 w) { atomicAdd(p, w); }
+__device__ __forceinline__ void add_val(uint32_t *p, u64 w) { atomicAdd((unsigned *)p, (unsigned)w); }
+
 template <typename ST>
 __device__ __forceinline__ bool better(ST sc, int32_t c, ST bsc, int32_t bc) {
   return c != INT32_MAX && (bc == INT32_MAX || sc > bsc || (sc == bsc && c < bc));
@@ -28,15 +38,16 @@ __device__ __forceinline__ bool better(ST sc, int32_t c, ST bsc, int32_t bc) {
 // Insert (c, w) into an open-addressing table of 2^log2H slots; the table has
 // at least twice as many slots as the row has entries, so it never fills.
 // Probing is bounded all the same: a full table sets *err and drops the entry.
-__device__ __forceinline__ void table_add(int32_t *keys, u64 *vals, int log2H, int32_t c, u64 w, u64 *err) {
+template <typename VT>
+__device__ __forceinline__ void table_add(int32_t *keys, VT *vals, int log2H, int32_t c, u64 w, u64 *err) {
   const uint32_t mask = (1u << log2H) - 1u;
   uint32_t s = hash32(c) >> (32 - log2H);
   for (uint32_t probe = 0; probe <= mask; probe++) {
     int32_t k = *(volatile int32_t *)&keys[s];
-    if (k == c) { atomicAdd(&vals[s], w); return; }
+    if (k == c) { add_val(&vals[s], w); return; }
     if (k == LEIDEN_EMPTY_KEY) {
       int32_t old = atomicCAS(&keys[s], LEIDEN_EMPTY_KEY, c);
-      if (old == LEIDEN_EMPTY_KEY || old == c) { atomicAdd(&vals[s], w); return; }
+      if (old == LEIDEN_EMPTY_KEY || old == c) { add_val(&vals[s], w); return; }
     }
     s = (s + 1) & mask;
   }
@@ -49,8 +60,8 @@ __device__ __forceinline__ void table_add(int32_t *keys, u64 *vals, int log2H, i
 // issued together, so the gathers overlap instead of running back to back.
 static constexpr int SCAN_UNROLL = LK_SCAN_UNROLL;
 static constexpr int ROW_UNROLL = LK_ROW_UNROLL;  // row entries per lane in flight in the decide kernels
-template <typename ST>
-__device__ __forceinline__ void scan_slots(const int32_t *keys, const u64 *vals, int H, int s0, int step,
+template <typename ST, typename VT>
+__device__ __forceinline__ void scan_slots(const int32_t *keys, const VT *vals, int H, int s0, int step,
                                            int32_t d, ST A, ST B, const int64_t *Sig, ST &bsc, int32_t &bc,
                                            int64_t &kid, int64_t &ncand) {
   for (int sb = s0; sb < H; sb += step * SCAN_UNROLL) {
@@ -132,8 +143,9 @@ __global__ void decide_group(MoveArgs<WT> a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = lane / G, gl = lane % G;
   const int leader = gw * G;
-  u64 *vals = reinterpret_cast<u64 *>(smem) + (size_t)(warp * GPW + gw) * H;
-  int32_t *keys = reinterpret_cast<int32_t *>(reinterpret_cast<u64 *>(smem) + (size_t)wpb * GPW * H) +
+  typedef typename TableVal<ST>::type VT;
+  VT *vals = reinterpret_cast<VT *>(smem) + (size_t)(warp * GPW + gw) * H;
+  int32_t *keys = reinterpret_cast<int32_t *>(reinterpret_cast<VT *>(smem) + (size_t)wpb * GPW * H) +
                   (size_t)(warp * GPW + gw) * H;
   __shared__ u64 wscratch[8][32];  // blocks of at most 256 threads
   u64 *wscr = wscratch[warp];
@@ -232,7 +244,7 @@ __global__ void decide_group(MoveArgs<WT> a) {
       if (act) {
         const ST A = (ST)a.A;
         const ST B = (ST)a.p * (ST)a.K[i];
-        scan_slots<ST>(keys, vals, 1 << lh, gl, G, d, A, B, a.Sig, bsc, bc, kid, ncand);
+        scan_slots<ST, VT>(keys, vals, 1 << lh, gl, G, d, A, B, a.Sig, bsc, bc, kid, ncand);
       }
     }
     if (act && gl == 0) { scanned += e1 - e0; nvert++; }
@@ -299,17 +311,18 @@ __global__ void decide_group(MoveArgs<WT> a) {
 // proportion to its row, not to the table size.
 // ---------------------------------------------------------------------------
 // Insert into a listed table: a newly occupied slot is appended to `used`.
-__device__ __forceinline__ void table_add_listed(int32_t *keys, u64 *vals, int log2H, int32_t c, u64 w,
+template <typename VT>
+__device__ __forceinline__ void table_add_listed(int32_t *keys, VT *vals, int log2H, int32_t c, u64 w,
                                                  uint16_t *used, unsigned *nused, u64 *err) {
   const uint32_t mask = (1u << log2H) - 1u;
   uint32_t s = hash32(c) >> (32 - log2H);
   for (uint32_t probe = 0; probe <= mask; probe++) {
     int32_t k = *(volatile int32_t *)&keys[s];
-    if (k == c) { atomicAdd(&vals[s], w); return; }
+    if (k == c) { add_val(&vals[s], w); return; }
     if (k == LEIDEN_EMPTY_KEY) {
       int32_t old = atomicCAS(&keys[s], LEIDEN_EMPTY_KEY, c);
       if (old == LEIDEN_EMPTY_KEY) used[atomicAdd(nused, 1u)] = (uint16_t)s;
-      if (old == LEIDEN_EMPTY_KEY || old == c) { atomicAdd(&vals[s], w); return; }
+      if (old == LEIDEN_EMPTY_KEY || old == c) { add_val(&vals[s], w); return; }
     }
     s = (s + 1) & mask;
   }
@@ -327,8 +340,9 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
   __shared__ int32_t s_mv;
   __shared__ unsigned s_nused;
   __shared__ u64 wscratch[32][32];
+  typedef typename TableVal<ST>::type VT;
   const int Hmax = 1 << log2H;
-  u64 *vals = reinterpret_cast<u64 *>(smem);
+  VT *vals = reinterpret_cast<VT *>(smem);
   int32_t *keys = reinterpret_cast<int32_t *>(vals + Hmax);
   uint16_t *used = reinterpret_cast<uint16_t *>(keys + Hmax);   // Hmax / 2 entries
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -536,7 +550,8 @@ template <int G, int LOG2H, bool REFINE, bool ASYNC, typename WT, typename ST>
 static void launch_group_k(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s) {
   auto k = decide_group<G, LOG2H, REFINE, ASYNC, WT, ST>;
   const int threads = t.threads;
-  const size_t smem = (size_t)(threads / 32) * (32 / G) * (1u << LOG2H) * (sizeof(u64) + sizeof(int32_t));
+  const size_t smem = (size_t)(threads / 32) * (32 / G) * (1u << LOG2H) *
+                      (sizeof(typename TableVal<ST>::type) + sizeof(int32_t));
   ensure_smem((const void *)k, smem);
   const int64_t groups_per_block = (threads / 32) * (32 / G);
   int64_t blocks = (a.list_n + groups_per_block - 1) / groups_per_block;
@@ -563,7 +578,8 @@ void launch_decide(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s
   if (t.kind != TIER_BLOCK) return;  // hub rows go through launch_hubs
   const int log2H = t.log2H;
   // table (value, key) plus the list of used slots (at most half the table)
-  const size_t smem = (size_t)(1u << log2H) * (sizeof(u64) + sizeof(int32_t)) + (size_t)(1u << log2H);
+  const size_t smem = (size_t)(1u << log2H) * (sizeof(typename TableVal<ST>::type) + sizeof(int32_t)) +
+                      (size_t)(1u << log2H);
   int64_t blocks = a.list_n;
   const int64_t cap = (int64_t)sms * 8;
   if (blocks > cap) blocks = cap;
@@ -592,6 +608,7 @@ TierTable default_tiers() {
   tt.t[k++] = {TIER_GROUP, 16, 16, 5, 256};
   tt.t[k++] = {TIER_GROUP, 32, 32, 6, 256};
   tt.t[k++] = {TIER_GROUP, 128, 32, 8, 256};
+  tt.t[k++] = {TIER_GROUP, 256, 32, 9, 256};
   tt.t[k++] = {TIER_GROUP, 512, 32, 10, 128};
   tt.t[k++] = {TIER_BLOCK, 2048, 0, 12, 256};
   tt.t[k++] = {TIER_BLOCK, 8192, 0, 14, 512};
