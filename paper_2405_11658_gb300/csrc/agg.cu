@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(512) agg_block_k(GraphView<WT> g, const int32_
 //            scratch it read.
 // No hash table lives in DRAM, so no atomic has to go there.
 // ---------------------------------------------------------------------------
-static constexpr int BUCKET_KEYS = 2048;      // expected distinct targets per bucket
+static constexpr int BUCKET_KEYS = 4096;      // at most this many distinct targets per bucket, on average
 static constexpr int64_t AGG_WINDOW = 512;    // flat entries per warp work item
 static constexpr uint32_t BUCKET_SLOTS = 6144;  // shared table of a bucket: 3x headroom
 
@@ -382,14 +382,39 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
 // One block per bucket: hash the bucket's pairs in shared memory, emit the
 // distinct targets into the community's hole range, reset the scratch.  The
 // table is cleared once per block; every bucket lists the slots it occupies
-// and resets exactly those while emitting them, so a bucket costs work in
-// proportion to its pairs, not to the table size.
+// (one shared atomic per warp) and resets exactly those while emitting them,
+// so a bucket costs work in proportion to its pairs, not to the table size.
+// A bucket reserves its output range with one global atomic, and thread 0
+// fetches the next bucket's description while the block emits.
 // Owner (index into the giant list) of every bucket, so a hashing block finds
 // its bucket's community with one load instead of a binary search.
 __global__ void agg_bown_k(const int64_t *bkoff, int64_t nlist, int32_t *bown) {
   GSTRIDE(k, nlist) {
     for (int64_t b = bkoff[k]; b < bkoff[k + 1]; b++) bown[b] = (int32_t)k;
   }
+}
+
+struct BucketInfo {
+  int64_t p0, p1;
+  int32_t c, lp;
+  u64 self;   // internal weight, if this bucket is the one key c falls in
+};
+
+__device__ __forceinline__ BucketInfo bucket_info(int64_t bk, const int32_t *list, const int32_t *bown,
+                                                  const int64_t *nbk, const int64_t *bkoff, const int64_t *bpos,
+                                                  const u64 *selfw) {
+  BucketInfo b;
+  const int32_t k = bown[bk];
+  b.p0 = bpos[bk];
+  b.p1 = bpos[bk + 1];
+  b.c = list[k];
+  const int64_t P = nbk[k];
+  int lp = 0;
+  while (((int64_t)1 << lp) < P) lp++;
+  b.lp = lp;
+  const u64 sw = selfw[k];
+  b.self = (sw && bk - bkoff[k] == bucket_of(b.c, P)) ? sw : 0;
+  return b;
 }
 
 __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, const int32_t *bown, const int64_t *nbk,
@@ -404,42 +429,48 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, const in
   uint16_t *used = reinterpret_cast<uint16_t *>(keys + H);
   __shared__ u64 wscratch[16][32];
   __shared__ int64_t s_ws;
-  __shared__ unsigned s_nused;
+  __shared__ unsigned s_nused, s_wcnt[16];
+  __shared__ int64_t s_base;
+  __shared__ BucketInfo s_b;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (uint32_t x = threadIdx.x; x < H; x += blockDim.x) { keys[x] = LEIDEN_EMPTY_KEY; vals[x] = 0; }
-  if (threadIdx.x == 0) s_nused = 0;
+  if (threadIdx.x == 0) {
+    s_nused = 0;
+    if (blockIdx.x < nb) s_b = bucket_info(blockIdx.x, list, bown, nbk, bkoff, bpos, selfw);
+  }
   for (int64_t bk = blockIdx.x; bk < nb; bk += gridDim.x) {
-    const int64_t k = bown[bk];
-    const int32_t c = list[k];
-    int lp = 0;
-    while (((int64_t)1 << lp) < nbk[k]) lp++;
-    const int64_t p0 = bpos[bk], p1 = bpos[bk + 1];
-    if (threadIdx.x == 0) s_ws = 0;
     __syncthreads();
+    const BucketInfo b = s_b;
+    const int32_t c = b.c;
+    const int lp = b.lp;
     // the bucket's keys share their top lp hash bits: index by the next ones
     // (scaled to the table size)
     auto home = [&](int32_t key) -> uint32_t {
       return (uint32_t)(((u64)(uint32_t)(hash32(key) << lp) * H) >> 32);
     };
     // the community's internal weight joins the bucket its own key falls in
-    if (threadIdx.x == 0 && selfw[k] && bk - bkoff[k] == bucket_of(c, nbk[k])) {
-      const uint32_t sl = home(c);   // the table is empty: the home slot is free
-      keys[sl] = c;
-      vals[sl] = selfw[k];
-      used[s_nused++] = (uint16_t)sl;
+    if (threadIdx.x == 0) {
+      s_ws = 0;
+      if (b.self) {
+        const uint32_t sl = home(c);   // the table is empty: the home slot is free
+        keys[sl] = c;
+        vals[sl] = b.self;
+        used[s_nused++] = (uint16_t)sl;
+      }
     }
     __syncthreads();
-    for (int64_t pb = p0 + 32 * warp; pb < p1; pb += 32 * (int64_t)nwarp) {  // warp-uniform
+    for (int64_t pb = b.p0 + 32 * warp; pb < b.p1; pb += 32 * (int64_t)nwarp) {  // warp-uniform
       const int64_t pos = pb + lane;
       int32_t d = LEIDEN_EMPTY_KEY;
       u64 w = 0;
-      if (pos < p1) {
+      if (pos < b.p1) {
         d = skeys[pos];
         w = svals[pos];
         skeys[pos] = LEIDEN_EMPTY_KEY;  // leave the scratch empty
         svals[pos] = 0;
       }
       u64 sum = 0;
+      int fresh = -1;
       if (warp_combine((unsigned long long)(uint32_t)d, d != LEIDEN_EMPTY_KEY, w, &sum, wscratch[warp])) {
         uint32_t sl = home(d);
         bool done = false;
@@ -448,35 +479,46 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, const in
           if (kk == d) { atomicAdd(&vals[sl], sum); done = true; }
           else if (kk == LEIDEN_EMPTY_KEY) {
             const int32_t old = atomicCAS(&keys[sl], LEIDEN_EMPTY_KEY, d);
-            if (old == LEIDEN_EMPTY_KEY) used[atomicAdd(&s_nused, 1u)] = (uint16_t)sl;
-            if (old == LEIDEN_EMPTY_KEY || old == d) { atomicAdd(&vals[sl], sum); done = true; }
+            if (old == LEIDEN_EMPTY_KEY || old == d) {
+              atomicAdd(&vals[sl], sum);
+              if (old == LEIDEN_EMPTY_KEY) fresh = (int)sl;
+              done = true;
+            }
           }
           sl = sl + 1 == H ? 0 : sl + 1;
         }
         if (!done) atomicOr(err, 16ull);
       }
+      // one shared atomic per warp for the slots it occupied
+      const unsigned m = __ballot_sync(FULL_MASK, fresh >= 0);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(&s_nused, (unsigned)__popc(m));
+        base = __shfl_sync(FULL_MASK, base, leader);
+        if (fresh >= 0) used[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)fresh;
+      }
     }
     __syncthreads();
     const unsigned nused = s_nused;
+    // the block's output range: one global atomic per bucket
+    if (threadIdx.x == 0) s_base = (int64_t)atomicAdd((u64 *)&cdist[c], (u64)nused);
+    // fetch the next bucket's description while the block emits
+    const int64_t nbk_next = bk + gridDim.x;
+    BucketInfo nx{};
+    if (threadIdx.x == 32 && nbk_next < nb) nx = bucket_info(nbk_next, list, bown, nbk, bkoff, bpos, selfw);
+    __syncthreads();
+    const int64_t out0 = hoff[c] + s_base;
     int64_t ws = 0;
-    for (unsigned u0 = 32 * warp; u0 < nused; u0 += 32 * nwarp) {  // warp-uniform
-      const unsigned u = u0 + lane;
-      const bool occ = u < nused;
-      int32_t key = LEIDEN_EMPTY_KEY;
-      int64_t v = 0;
-      if (occ) {
-        const uint32_t sl = used[u];
-        key = keys[sl];
-        v = (int64_t)vals[sl];
-        keys[sl] = LEIDEN_EMPTY_KEY;   // reset on read: clean for the next bucket
-        vals[sl] = 0;
-      }
-      const u64 slot = warp_reserve((u64 *)&cdist[c], occ);
-      if (occ) {
-        hidx[hoff[c] + (int64_t)slot] = key;
-        hw[hoff[c] + (int64_t)slot] = v;
-        ws += v;
-      }
+    for (unsigned u = threadIdx.x; u < nused; u += blockDim.x) {
+      const uint32_t sl = used[u];
+      const int32_t key = keys[sl];
+      const int64_t v = (int64_t)vals[sl];
+      keys[sl] = LEIDEN_EMPTY_KEY;   // reset on read: clean for the next bucket
+      vals[sl] = 0;
+      hidx[out0 + u] = key;
+      hw[out0 + u] = v;
+      ws += v;
     }
     for (int o = 16; o; o >>= 1) ws += shfl_xor_i64(ws, o);
     if (lane == 0 && ws) atomicAdd((u64 *)&s_ws, (u64)ws);
@@ -485,7 +527,7 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, const in
       if (s_ws) atomicAdd((u64 *)&Kout[c], (u64)s_ws);
       s_nused = 0;
     }
-    __syncthreads();
+    if (threadIdx.x == 32) s_b = nx;
   }
 }
 

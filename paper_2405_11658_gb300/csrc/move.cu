@@ -310,23 +310,39 @@ __global__ void decide_group(MoveArgs<WT> a) {
 // scan resets exactly those while reading them, so a vertex costs work in
 // proportion to its row, not to the table size.
 // ---------------------------------------------------------------------------
-// Insert into a listed table: a newly occupied slot is appended to `used`.
+// Insert into a table; returns the slot if this call occupied it (else -1),
+// so the caller can list the table's occupied slots.
 template <typename VT>
-__device__ __forceinline__ void table_add_listed(int32_t *keys, VT *vals, int log2H, int32_t c, u64 w,
-                                                 uint16_t *used, unsigned *nused, u64 *err) {
+__device__ __forceinline__ int table_add_new(int32_t *keys, VT *vals, int log2H, int32_t c, u64 w, u64 *err) {
   const uint32_t mask = (1u << log2H) - 1u;
   uint32_t s = hash32(c) >> (32 - log2H);
   for (uint32_t probe = 0; probe <= mask; probe++) {
     int32_t k = *(volatile int32_t *)&keys[s];
-    if (k == c) { add_val(&vals[s], w); return; }
+    if (k == c) { add_val(&vals[s], w); return -1; }
     if (k == LEIDEN_EMPTY_KEY) {
       int32_t old = atomicCAS(&keys[s], LEIDEN_EMPTY_KEY, c);
-      if (old == LEIDEN_EMPTY_KEY) used[atomicAdd(nused, 1u)] = (uint16_t)s;
-      if (old == LEIDEN_EMPTY_KEY || old == c) { add_val(&vals[s], w); return; }
+      if (old == LEIDEN_EMPTY_KEY || old == c) {
+        add_val(&vals[s], w);
+        return old == LEIDEN_EMPTY_KEY ? (int)s : -1;
+      }
     }
     s = (s + 1) & mask;
   }
   atomicOr(err, 16ull);
+  return -1;
+}
+
+// Appends the slots the warp's lanes newly occupied to the used-slot list with
+// one shared atomic per warp (a per-lane atomic on one counter serialises the
+// whole block).  The whole warp must call.
+__device__ __forceinline__ void list_new_slots(int slot, uint16_t *used, unsigned *nused) {
+  const unsigned m = __ballot_sync(FULL_MASK, slot >= 0);
+  if (!m) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (lane == leader) base = atomicAdd(nused, (unsigned)__popc(m));
+  base = __shfl_sync(FULL_MASK, base, leader);
+  if (slot >= 0) used[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)slot;
 }
 
 template <bool REFINE, bool ASYNC, typename WT, typename ST>
@@ -391,9 +407,11 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
 #pragma unroll
       for (int u = 0; u < ROW_UNROLL; u++) {
         u64 sum = 0;
+        int slot = -1;
         if (warp_combine((unsigned long long)(uint32_t)cc[u], cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum,
                          wscratch[warp]))
-          table_add_listed(keys, vals, lh, cc[u], sum, used, &s_nused, &a.ctr[CTR_ERROR]);
+          slot = table_add_new(keys, vals, lh, cc[u], sum, &a.ctr[CTR_ERROR]);
+        list_new_slots(slot, used, &s_nused);
       }
     }
     if (threadIdx.x == 0) { scanned += e1 - e0; nvert++; }

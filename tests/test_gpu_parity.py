@@ -291,7 +291,11 @@ def test_self_loops_in_input(ctx):
 # schedules on the structured families; on the hub-heavy ones (a few rows of
 # 10^4 entries next to thousands of short rows, weighted Chung-Lu) run-to-run
 # spread reaches a few 1e-3, so the bar there is 1e-2.
-ASYNC_TOL = {"pp_1e4": 1e-3, "pp_strong": 1e-3, "rmat14": 1e-3, "grid": 1e-3,
+# 1e-3 on graphs with clear community structure.  R-MAT's weak structure
+# leaves many near-equal local optima -- on rmat14 the oracle's own DET and
+# GS schedules end 7e-3 apart -- and in-place commits land in a different one
+# from run to run, as do the hub-dominated graphs.
+ASYNC_TOL = {"pp_1e4": 1e-3, "pp_strong": 1e-3, "grid": 1e-3, "rmat14": 5e-3,
              "chung_lu_w": 1e-2, "hubs": 1e-2}
 
 
