@@ -67,6 +67,51 @@ __device__ __forceinline__ void tadd(int32_t *keys, u64 *vals, uint32_t mask, in
   atomicOr(err, 16ull);
 }
 
+// Flattened walk over the row segments of a warp's lanes: lane l holds a
+// segment of cnt entries starting at CSR position rs, incl is the inclusive
+// prefix of cnt over the lanes and total its sum.  The warp visits the
+// segments' entries 32 at a time, AGG_UNROLL batches in flight (their idx and
+// C' loads issued before the first is used), and calls f(target, weight,
+// active) warp-uniformly for each batch.
+static constexpr int AGG_UNROLL = 4;
+template <typename WT, typename F>
+__device__ __forceinline__ void walk_segments(const GraphView<WT> &g, const int32_t *C, int64_t rs, int64_t cnt,
+                                              int64_t incl, int64_t total, u64 *err, F f) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t t0 = 0; t0 < total; t0 += 32 * AGG_UNROLL) {  // uniform per warp
+    int32_t jj[AGG_UNROLL];
+    u64 wv[AGG_UNROLL];
+#pragma unroll
+    for (int u = 0; u < AGG_UNROLL; u++) {
+      const int64_t t = t0 + 32 * u + lane;
+      // first lane whose inclusive sum exceeds t
+      int k = 0;
+#pragma unroll
+      for (int b = 16; b; b >>= 1) {
+        const int64_t v = shfl_i64(incl, k + b - 1);
+        if (v <= t) k += b;
+      }
+      const int64_t sk = shfl_i64(rs, k), ik = shfl_i64(incl, k), dk = shfl_i64(cnt, k);
+      jj[u] = -1;
+      wv[u] = 0;
+      if (t < total) {
+        const int64_t e = sk + (t - (ik - dk));
+        if (e >= sk && e < sk + dk) { jj[u] = g.idx[e]; wv[u] = (u64)(int64_t)g.w[e]; }
+        else atomicOr(err, 64ull);
+      }
+    }
+    int32_t cc[AGG_UNROLL];
+#pragma unroll
+    for (int u = 0; u < AGG_UNROLL; u++) {
+      const bool ok = (uint32_t)jj[u] < (uint32_t)g.n;
+      if (!ok && jj[u] != -1) atomicOr(err, 64ull);
+      cc[u] = ok ? C[jj[u]] : LEIDEN_EMPTY_KEY;
+    }
+#pragma unroll
+    for (int u = 0; u < AGG_UNROLL; u++) f(cc[u], wv[u], cc[u] != LEIDEN_EMPTY_KEY);
+  }
+}
+
 // The warp walks the rows of members cv[m0 .. m1) as one flattened range:
 // each batch of 32 members is prefix-summed across the lanes, and every lane
 // finds the member of its entry by a binary search over the shuffled sums.
@@ -91,30 +136,10 @@ __device__ __forceinline__ void warp_rows_into_table(const GraphView<WT> &g, con
       if (lane >= o) incl += y;
     }
     const int64_t total = shfl_i64(incl, 31);
-    for (int64_t t0 = 0; t0 < total; t0 += 32) {
-      const int64_t t = t0 + lane;
-      // first lane whose inclusive sum exceeds t
-      int k = 0;
-#pragma unroll
-      for (int b = 16; b; b >>= 1) {
-        const int64_t v = shfl_i64(incl, k + b - 1);
-        if (v <= t) k += b;
-      }
-      const int64_t sk = shfl_i64(start, k);
-      const int64_t ik = shfl_i64(incl, k);
-      const int64_t dk = shfl_i64(deg, k);
-      int32_t c = LEIDEN_EMPTY_KEY;
-      u64 wv = 0;
-      if (t < total) {
-        const int64_t e = sk + (t - (ik - dk));
-        const int32_t j = (e >= sk && e < sk + dk) ? g.idx[e] : -1;
-        if ((uint32_t)j < (uint32_t)g.n) { c = C[j]; wv = (u64)(int64_t)g.w[e]; }
-        else atomicOr(err, 64ull);
-      }
+    walk_segments(g, C, start, deg, incl, total, err, [&](int32_t c, u64 wv, bool act) {
       u64 sum = 0;
-      if (warp_combine((unsigned long long)(uint32_t)c, c != LEIDEN_EMPTY_KEY, wv, &sum, scratch))
-        tadd(keys, vals, mask, sh, c, sum, err);
-    }
+      if (warp_combine((unsigned long long)(uint32_t)c, act, wv, &sum, scratch)) tadd(keys, vals, mask, sh, c, sum, err);
+    });
   }
 }
 
@@ -226,6 +251,7 @@ __global__ void __launch_bounds__(512) agg_block_k(GraphView<WT> g, const int32_
 static constexpr int BUCKET_KEYS = 4096;      // at most this many distinct targets per bucket, on average
 static constexpr int64_t AGG_WINDOW = 512;    // flat entries per warp work item
 static constexpr uint32_t BUCKET_SLOTS = 6144;  // shared table of a bucket: 3x headroom
+static constexpr int BH_UNROLL = 4;              // chunks of 32 pairs in flight per warp
 
 __global__ void agg_bsize_k(const int32_t *list, int64_t nlist, const int64_t *hoff, int64_t nc, int64_t *nbk,
                             int64_t *nwin) {
@@ -283,25 +309,7 @@ __device__ __forceinline__ void foreach_window(const GraphView<WT> &g, const int
       if (lane >= o) incl += y;
     }
     const int64_t total = shfl_i64(incl, 31);
-    for (int64_t t0 = 0; t0 < total; t0 += 32) {
-      const int64_t t = t0 + lane;
-      int k = 0;
-#pragma unroll
-      for (int b = 16; b; b >>= 1) {
-        const int64_t v = shfl_i64(incl, k + b - 1);
-        if (v <= t) k += b;
-      }
-      const int64_t sk = shfl_i64(rs, k), ik = shfl_i64(incl, k), dk = shfl_i64(cnt, k);
-      int32_t c = LEIDEN_EMPTY_KEY;
-      u64 wv = 0;
-      if (t < total) {
-        const int64_t e = sk + (t - (ik - dk));
-        const int32_t j = (e >= sk && e < sk + dk) ? g.idx[e] : -1;
-        if ((uint32_t)j < (uint32_t)g.n) { c = C[j]; wv = (u64)(int64_t)g.w[e]; }
-        else atomicOr(err, 64ull);
-      }
-      f(c, wv, c != LEIDEN_EMPTY_KEY);
-    }
+    walk_segments(g, C, rs, cnt, incl, total, err, f);
   }
 }
 
@@ -459,44 +467,56 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, const in
       }
     }
     __syncthreads();
-    for (int64_t pb = b.p0 + 32 * warp; pb < b.p1; pb += 32 * (int64_t)nwarp) {  // warp-uniform
-      const int64_t pos = pb + lane;
-      int32_t d = LEIDEN_EMPTY_KEY;
-      u64 w = 0;
-      if (pos < b.p1) {
-        d = skeys[pos];
-        w = svals[pos];
-        skeys[pos] = LEIDEN_EMPTY_KEY;  // leave the scratch empty
-        svals[pos] = 0;
+    // BH_UNROLL chunks of 32 pairs per warp iteration: their loads are all in
+    // flight before the first is hashed (one chunk at a time leaves the loop
+    // waiting on memory latency)
+    for (int64_t pb0 = b.p0 + 32 * BH_UNROLL * warp; pb0 < b.p1; pb0 += 32 * BH_UNROLL * (int64_t)nwarp) {
+      int32_t dd[BH_UNROLL];
+      u64 ww[BH_UNROLL];
+#pragma unroll
+      for (int u = 0; u < BH_UNROLL; u++) {
+        const int64_t pos = pb0 + 32 * u + lane;
+        dd[u] = LEIDEN_EMPTY_KEY;
+        ww[u] = 0;
+        if (pos < b.p1) { dd[u] = skeys[pos]; ww[u] = svals[pos]; }
       }
-      u64 sum = 0;
-      int fresh = -1;
-      if (warp_combine((unsigned long long)(uint32_t)d, d != LEIDEN_EMPTY_KEY, w, &sum, wscratch[warp])) {
-        uint32_t sl = home(d);
-        bool done = false;
-        for (uint32_t probe = 0; probe < H && !done; probe++) {
-          const int32_t kk = *(volatile int32_t *)&keys[sl];
-          if (kk == d) { atomicAdd(&vals[sl], sum); done = true; }
-          else if (kk == LEIDEN_EMPTY_KEY) {
-            const int32_t old = atomicCAS(&keys[sl], LEIDEN_EMPTY_KEY, d);
-            if (old == LEIDEN_EMPTY_KEY || old == d) {
-              atomicAdd(&vals[sl], sum);
-              if (old == LEIDEN_EMPTY_KEY) fresh = (int)sl;
-              done = true;
+#pragma unroll
+      for (int u = 0; u < BH_UNROLL; u++) {
+        const int64_t pos = pb0 + 32 * u + lane;
+        if (pos < b.p1) { skeys[pos] = LEIDEN_EMPTY_KEY; svals[pos] = 0; }  // leave the scratch empty
+      }
+#pragma unroll
+      for (int u = 0; u < BH_UNROLL; u++) {
+        const int32_t d = dd[u];
+        u64 sum = 0;
+        int fresh = -1;
+        if (warp_combine((unsigned long long)(uint32_t)d, d != LEIDEN_EMPTY_KEY, ww[u], &sum, wscratch[warp])) {
+          uint32_t sl = home(d);
+          bool done = false;
+          for (uint32_t probe = 0; probe < H && !done; probe++) {
+            const int32_t kk = *(volatile int32_t *)&keys[sl];
+            if (kk == d) { atomicAdd(&vals[sl], sum); done = true; }
+            else if (kk == LEIDEN_EMPTY_KEY) {
+              const int32_t old = atomicCAS(&keys[sl], LEIDEN_EMPTY_KEY, d);
+              if (old == LEIDEN_EMPTY_KEY || old == d) {
+                atomicAdd(&vals[sl], sum);
+                if (old == LEIDEN_EMPTY_KEY) fresh = (int)sl;
+                done = true;
+              }
             }
+            sl = sl + 1 == H ? 0 : sl + 1;
           }
-          sl = sl + 1 == H ? 0 : sl + 1;
+          if (!done) atomicOr(err, 16ull);
         }
-        if (!done) atomicOr(err, 16ull);
-      }
-      // one shared atomic per warp for the slots it occupied
-      const unsigned m = __ballot_sync(FULL_MASK, fresh >= 0);
-      if (m) {
-        const int leader = __ffs(m) - 1;
-        unsigned base = 0;
-        if (lane == leader) base = atomicAdd(&s_nused, (unsigned)__popc(m));
-        base = __shfl_sync(FULL_MASK, base, leader);
-        if (fresh >= 0) used[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)fresh;
+        // one shared atomic per warp for the slots it occupied
+        const unsigned m = __ballot_sync(FULL_MASK, fresh >= 0);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          unsigned base = 0;
+          if (lane == leader) base = atomicAdd(&s_nused, (unsigned)__popc(m));
+          base = __shfl_sync(FULL_MASK, base, leader);
+          if (fresh >= 0) used[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)fresh;
+        }
       }
     }
     __syncthreads();

@@ -59,7 +59,8 @@ __device__ __forceinline__ void table_add(int32_t *keys, VT *vals, int log2H, in
 // d.  SCAN_UNROLL slots per lane are loaded first and their Sigma'[c] gathers
 // issued together, so the gathers overlap instead of running back to back.
 static constexpr int SCAN_UNROLL = LK_SCAN_UNROLL;
-static constexpr int ROW_UNROLL = LK_ROW_UNROLL;  // row entries per lane in flight in the decide kernels
+static constexpr int ROW_UNROLL = LK_ROW_UNROLL;  // row entries per lane in flight in the group kernels
+static constexpr int BLOCK_ROW_UNROLL = 1;        // ... and in the block kernels (4 measured slower)
 template <typename ST, typename VT>
 __device__ __forceinline__ void scan_slots(const int32_t *keys, const VT *vals, int H, int s0, int step,
                                            int32_t d, ST A, ST B, const int64_t *Sig, ST &bsc, int32_t &bc,
@@ -384,11 +385,11 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
     const int32_t cbi = REFINE ? a.CB[i] : 0;
     // each warp walks 32-entry chunks (warp-uniform), combining equal
     // communities across its lanes before the atomics
-    for (int64_t cb = e0 + 32 * warp; cb < e1; cb += 32 * (int64_t)nwarp * ROW_UNROLL) {
-      int32_t cc[ROW_UNROLL];
-      u64 wv[ROW_UNROLL];
+    for (int64_t cb = e0 + 32 * warp; cb < e1; cb += 32 * (int64_t)nwarp * BLOCK_ROW_UNROLL) {
+      int32_t cc[BLOCK_ROW_UNROLL];
+      u64 wv[BLOCK_ROW_UNROLL];
 #pragma unroll
-      for (int u = 0; u < ROW_UNROLL; u++) {
+      for (int u = 0; u < BLOCK_ROW_UNROLL; u++) {
         const int64_t e = cb + (int64_t)u * 32 * nwarp + lane;
         const bool in = e < e1;
         const int32_t j = in ? a.g.idx[e] : -1;
@@ -398,14 +399,14 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
         cc[u] = ok ? j : -1;
       }
 #pragma unroll
-      for (int u = 0; u < ROW_UNROLL; u++) {
+      for (int u = 0; u < BLOCK_ROW_UNROLL; u++) {
         const int32_t j = cc[u];
         bool ok = j >= 0;
         if (REFINE && ok && a.CB[j] != cbi) ok = false;
         cc[u] = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
       }
 #pragma unroll
-      for (int u = 0; u < ROW_UNROLL; u++) {
+      for (int u = 0; u < BLOCK_ROW_UNROLL; u++) {
         u64 sum = 0;
         int slot = -1;
         if (warp_combine((unsigned long long)(uint32_t)cc[u], cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum,
