@@ -285,13 +285,25 @@ __global__ void __launch_bounds__(256) hub_final_k(MoveArgs<WT> a, HubWork hw) {
 // every listed row, so one long row is spread over the whole grid.
 __global__ void __launch_bounds__(256) mark_big_rows_k(const int32_t *big, const u64 *count, const int64_t *off,
                                                        const int32_t *idx, uint8_t *processed) {
+  // bpr blocks per row: the whole grid on one row when there are few rows,
+  // one block per row (rows strided over the grid) when there are many
   const u64 nb = *count;
-  for (u64 m = 0; m < nb; m++) {
+  if (nb == 0) return;
+  const u64 bpr = gridDim.x / nb > 0 ? gridDim.x / nb : 1;
+  const u64 rows_at_once = gridDim.x / bpr;
+  const u64 part = blockIdx.x % bpr;
+  for (u64 m = blockIdx.x / bpr; m < nb && blockIdx.x < rows_at_once * bpr; m += rows_at_once) {
     const int32_t i = big[m];
     const int64_t e0 = off[i], e1 = off[i + 1];
-    for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
-         e += (int64_t)gridDim.x * blockDim.x)
-      processed[idx[e]] = 0;
+    const int64_t step = (int64_t)bpr * blockDim.x;
+    for (int64_t e = e0 + (int64_t)part * blockDim.x + threadIdx.x; e < e1; e += 4 * step) {
+      int32_t j[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) j[u] = e + u * step < e1 ? idx[e + u * step] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        if (j[u] >= 0) processed[j[u]] = 0;
+    }
   }
 }
 

@@ -502,27 +502,39 @@ __global__ void __launch_bounds__(256) apply_moves_k(const int32_t *prop_i, cons
   __shared__ i128 sbuf[32];
   const u64 cnt = ctr[CTR_PROPS];
   const int lane = threadIdx.x & 31;
-  const u64 wglob = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const u64 nw = ((u64)gridDim.x * blockDim.x) >> 5;
+  const u64 gt = (u64)blockIdx.x * blockDim.x + threadIdx.x, nt = (u64)gridDim.x * blockDim.x;
   i128 acc = 0;
-  for (u64 m = wglob; m < cnt; m += nw) {
+  // commits: one thread per proposal (the vertex's own entries only)
+  for (u64 m = gt; m < cnt; m += nt) {
     const int32_t i = prop_i[m], c = prop_c[m];
-    if (lane == 0) {
-      const int32_t d = C[i];
-      const int64_t Ki = K[i];
-      atomic_add_i64(&Sig[d], -Ki);
-      atomic_add_i64(&Sig[c], Ki);
-      C[i] = c;
-      if (dynamic) { changed[d] = 1; changed[c] = 1; }
-      acc += prop_S[m];
-    }
-    // vertex pruning: a mover re-marks its neighbours (long rows are left to
-    // the big-row kernel, which spreads them over the grid)
-    const int64_t e0 = off[i], e1 = off[i + 1];
+    const int32_t d = C[i];
+    const int64_t Ki = K[i];
+    atomic_add_i64(&Sig[d], -Ki);
+    atomic_add_i64(&Sig[c], Ki);
+    C[i] = c;
+    if (dynamic) { changed[d] = 1; changed[c] = 1; }
+    acc += prop_S[m];
+  }
+  // vertex pruning: a mover re-marks its neighbours, half a warp per mover
+  // with four row loads in flight (independent of the commits above; long
+  // rows are left to the big-row kernel, which spreads them over the grid)
+  const u64 hw_glob = gt >> 4, nhw = nt >> 4;
+  const int hl = lane & 15;
+  for (u64 m = hw_glob; m < cnt; m += nhw) {
+    const int32_t i = prop_i[m];
+    const int64_t e0 = off[i];
+    int64_t e1 = off[i + 1];
     if (e1 - e0 > BIG_ROW) {
-      if (lane == 0) big[atomicAdd(&ctr[CTR_BIG], 1ull)] = i;
-    } else {
-      for (int64_t e = e0 + lane; e < e1; e += 32) processed[idx[e]] = 0;
+      if (hl == 0) big[atomicAdd(&ctr[CTR_BIG], 1ull)] = i;
+      e1 = e0;
+    }
+    for (int64_t e = e0 + hl; e < e1; e += 64) {
+      int32_t j[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) j[u] = e + 16 * u < e1 ? idx[e + 16 * u] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        if (j[u] >= 0) processed[j[u]] = 0;
     }
   }
   const i128 tot = block_sum_i128(acc, sbuf);
