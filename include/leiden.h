@@ -227,9 +227,9 @@ typedef struct leiden_batch leiden_batch;
  * legacy default stream) for up to max_graphs graphs per run with at most
  * max_total_n vertices and max_total_nnz CSR entries summed over the run's
  * graphs (about 300 B per vertex plus 36 B per entry).  `threads` is the
- * block size of the persistent kernel (128..512, multiple of 32; 0 = 256)
+ * block size of the persistent kernel (128..512, multiple of 32; 0 = 512)
  * and blocks_per_sm the number of blocks per SM it is launched with (1..4;
- * 0 = 2).  Errors: LEIDEN_EINVAL, LEIDEN_ENOMEM, LEIDEN_ECUDA. */
+ * 0 = 1).  Errors: LEIDEN_EINVAL, LEIDEN_ENOMEM, LEIDEN_ECUDA. */
 int leiden_batch_create(leiden_batch **out, void *cuda_stream, int32_t max_graphs, int64_t max_total_n,
                         int64_t max_total_nnz, int32_t threads, int32_t blocks_per_sm);
 
@@ -314,7 +314,9 @@ typedef struct {
                               * candidate tier tables and use its table for the graph's runs */
   int32_t small_workers;     /* workers for small graphs, each with its own persistent launch in
                               * flight (>= 1; 0 = 2) */
-  int32_t reserved;          /* must be 0 */
+  int32_t min_persistent;    /* fewer ready small graphs than this run one by one on the worker's
+                              * context (all SMs on one graph) instead of one persistent launch
+                              * (one block per graph); 0 = 8 */
   leiden_opts opts;          /* DET schedule */
 } leiden_server_config;
 
@@ -348,7 +350,8 @@ int leiden_server_submit(leiden_server *s, int32_t graph_id, const leiden_edges 
 typedef struct {
   int32_t status;            /* LEIDEN_OK or the request's error */
   int32_t graph;
-  int32_t path;              /* 0: persistent many-graph launch, 1: large-graph worker */
+  int32_t path;              /* 0: persistent many-graph launch, 1: large-graph worker,
+                              * 2: small-graph worker on its own context (few graphs ready) */
   int32_t launch_graphs;     /* graphs in the same persistent launch (path 0) */
   double q;                  /* modularity of the new membership */
   double queue_ms;           /* submission to start of its work */

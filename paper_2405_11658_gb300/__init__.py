@@ -137,7 +137,7 @@ class _ServerConfig(C.Structure):
                 ("large_max_n", C.c_int64), ("large_max_nnz", C.c_int64), ("small_max_n", C.c_int64),
                 ("small_max_nnz", C.c_int64), ("small_batch_n", C.c_int64), ("small_batch_nnz", C.c_int64),
                 ("growth", C.c_double), ("mode", C.c_int32), ("autotune_trials", C.c_int32),
-                ("small_workers", C.c_int32), ("reserved", C.c_int32), ("opts", _Opts)]
+                ("small_workers", C.c_int32), ("min_persistent", C.c_int32), ("opts", _Opts)]
 
 
 class _RequestInfo(C.Structure):

@@ -206,9 +206,52 @@ void run_large(leiden_server *s, int k, Resident *g, Request *r) {
   finish(s, g, d);
 }
 
+// A small graph's request on the small worker's own context (all SMs on one
+// graph): for the few-graph case, where one block per graph would be slower.
+void run_small_alone(leiden_server *s, int w, Resident *g, Request *r) {
+  leiden_server::Small &sw = s->small[w];
+  leiden_request_info &info = r->info;
+  info.graph = g->id;
+  info.path = 2;
+  int rc = LEIDEN_OK;
+  double q = 0.0;
+  const int mx = 1 - g->mem;
+  if (r->is_static) {
+    leiden_csr c = csr_of(*g, g->csr, g->nnz);
+    rc = leiden_static(sw.ctx, &c, &s->cfg.opts, g->C[mx], &q);
+    if (!rc) { g->mem = mx; g->has_aux = false; }
+  } else {
+    rc = grow(s, sw.stage, batch_words(*r));
+    leiden_edges del{}, ins{};
+    if (!rc) upload_batch(*r, sw.stage.buf, sw.st, &del, &ins);
+    int64_t nnz2 = 0;
+    const int nx = 1 - g->csr;
+    leiden_csr cur = csr_of(*g, g->csr, g->nnz);
+    if (!rc) rc = leiden_apply_batch(sw.ctx, &cur, &del, &ins, g->off[nx], g->idx[nx], g->w[nx], g->cap, &nnz2);
+    if (!rc) {
+      leiden_csr nxt = csr_of(*g, nx, nnz2);
+      rc = leiden_update(sw.ctx, &nxt, g->C[g->mem], g->has_aux ? g->K[g->mem] : nullptr,
+                         g->has_aux ? g->Sig[g->mem] : nullptr, &del, &ins, s->cfg.mode, &s->cfg.opts, g->C[mx],
+                         g->K[mx], g->Sig[mx], &q);
+      if (!rc) { g->csr = nx; g->nnz = nnz2; g->mem = mx; g->has_aux = true; }
+    }
+  }
+  cudaStreamSynchronize(sw.st);
+  info.status = rc;
+  info.q = q;
+  info.n = g->n;
+  info.nnz = g->nnz;
+  std::vector<Request *> d{r};
+  finish(s, g, d);
+}
+
 // The ready requests of small graphs, in one persistent launch.
 void run_small(leiden_server *s, int w, std::vector<std::pair<Resident *, Request *>> &work) {
   leiden_server::Small &sw = s->small[w];
+  if ((int)work.size() < s->cfg.min_persistent) {
+    for (auto &x : work) run_small_alone(s, w, x.first, x.second);
+    return;
+  }
   cudaStream_t st = sw.st;
   int64_t words = 0;
   for (auto &x : work) words += batch_words(*x.second);
@@ -374,7 +417,8 @@ extern "C" int leiden_server_create(leiden_server **out, const leiden_server_con
   if (c.mode == 0) c.mode = LEIDEN_DF;
   if (c.mode != LEIDEN_DF && c.mode != LEIDEN_ND) return LEIDEN_EINVAL;
   if (c.small_workers == 0) c.small_workers = 2;
-  if (c.small_workers < 1 || c.small_workers > 8 || c.reserved) return LEIDEN_EINVAL;
+  if (c.min_persistent == 0) c.min_persistent = 8;
+  if (c.small_workers < 1 || c.small_workers > 8 || c.min_persistent < 1) return LEIDEN_EINVAL;
   if (c.large_slots < 1 || c.large_slots > 16 || c.small_max_graphs < 1 || c.autotune_trials < 0) return LEIDEN_EINVAL;
   if (c.hbm_budget <= 0 || c.large_max_n < 1 || c.large_max_nnz < 1 || c.small_max_n < 1 || c.small_max_nnz < 1)
     return LEIDEN_EINVAL;

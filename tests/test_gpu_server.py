@@ -71,9 +71,10 @@ def expected():
     return graphs, seqs, [oracle_sequence(g, b) for g, b in zip(graphs, seqs)]
 
 
-def test_server_results_match_the_oracle_in_the_mix(expected):
+@pytest.mark.parametrize("min_persistent", [1, 64])    # 64: every small graph runs alone on its worker's context
+def test_server_results_match_the_oracle_in_the_mix(expected, min_persistent):
     graphs, seqs, want = expected
-    with L.Server(**CFG) as srv:
+    with L.Server(**dict(CFG, min_persistent=min_persistent)) as srv:
         ids, reqs = [], []
         for g in graphs:
             gid, rid = srv.admit(*g)
@@ -99,10 +100,10 @@ def test_server_results_match_the_oracle_in_the_mix(expected):
                 paths.add(info["path"])
             memb = srv.membership(ids[k], len(g[0]) - 1)
             assert np.array_equal(memb, want[k][-1][0]), k
-        assert paths == {0, 1}
+        assert paths == ({0, 1} if min_persistent == 1 else {1, 2})
         st = srv.stats()
         assert st["completed"] == sum(len(r) for r in reqs) and st["failed"] == 0
-        assert st["small_launches"] >= 1 and st["large_runs"] >= 1
+        assert st["large_runs"] >= 1 and (st["small_launches"] >= 1) == (min_persistent == 1)
 
 
 def test_server_result_alone_equals_result_in_the_mix(expected):
