@@ -515,7 +515,7 @@ def run_serving(args):
     ok = [x for x in infos if x[2]["status"] == 0]
     lat = np.array([x[2]["latency_ms"] for x in ok])
     per_path = {}
-    for path, name in ((0, "persistent"), (1, "large")):
+    for path, name in ((0, "persistent"), (1, "large"), (2, "small_alone")):
         v = np.array([x[2]["latency_ms"] for x in ok if x[2]["path"] == path])
         if len(v):
             per_path[name] = {"requests": int(len(v)), "p50_ms": float(np.percentile(v, 50)),
