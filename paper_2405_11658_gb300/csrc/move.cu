@@ -61,6 +61,8 @@ __device__ __forceinline__ void table_add(int32_t *keys, VT *vals, int log2H, in
 static constexpr int SCAN_UNROLL = LK_SCAN_UNROLL;
 static constexpr int ROW_UNROLL = LK_ROW_UNROLL;  // row entries per lane in flight in the group kernels
 static constexpr int BLOCK_ROW_UNROLL = 1;        // ... and in the block kernels (4 measured slower)
+// Vertices per SM below which a whole-warp group tier runs as 4-warp blocks.
+static constexpr int64_t SMALL_WAVE_VERTICES = 16;
 template <typename ST, typename VT>
 __device__ __forceinline__ void scan_slots(const int32_t *keys, const VT *vals, int H, int s0, int step,
                                            int32_t d, ST A, ST B, const int64_t *Sig, ST &bsc, int32_t &bc,
@@ -595,6 +597,15 @@ static void launch_group_k(const Tier &t, const MoveArgs<WT> &a, int sms, cudaSt
 template <typename WT, typename ST, bool REFINE, bool ASYNC>
 void launch_decide(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s) {
   if (a.list_n <= 0) return;
+  // A whole-warp group tier with rows of more than 64 entries and too few
+  // vertices to fill the GPU runs in a single wave, so its time is one
+  // vertex's latency: give each vertex a block of four warps instead (same
+  // decisions, a quarter of the per-vertex steps).
+  if (t.kind == TIER_GROUP && t.G == 32 && t.log2H >= 8 && a.list_n <= (int64_t)sms * SMALL_WAVE_VERTICES) {
+    const Tier b{TIER_BLOCK, t.maxdeg, 0, t.log2H, 128};
+    launch_decide<WT, ST, REFINE, ASYNC>(b, a, sms, s);
+    return;
+  }
   if (t.kind == TIER_GROUP) {
 #define LK_GROUP(GG, LH)                                                        \
   if (t.G == GG && t.log2H == LH) {                                             \
