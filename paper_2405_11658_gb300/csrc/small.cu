@@ -30,6 +30,7 @@ namespace lk {
 namespace {
 
 constexpr int SB_WARP_SLOTS = 256;   // shared-memory slots per warp
+constexpr int SB_GROUP_ROW = 32;     // rows up to this long go to 8-lane groups (64-slot tables)
 constexpr int SB_MAX_WARPS = 32;
 constexpr int SB_MAX_CLASSES = 256;
 
@@ -68,7 +69,7 @@ struct Shared {
   int job;
   int stop;
   u64 err;
-  unsigned nprop, nlong;
+  unsigned nprop, nlong, nmed;
   int64_t long_n;
   int32_t koff[SB_MAX_CLASSES + 1];
   int32_t kcur[SB_MAX_CLASSES];
@@ -201,32 +202,120 @@ __device__ void carve_ws(char *base, int64_t n, int64_t nnz, WS &w) {
 // (REFINE = false) or refinement (REFINE = true).  Proposals go to
 // (pi, pc, pS)[0 .. sm.nprop).
 // ---------------------------------------------------------------------------
+// Proposal of vertex i (one thread): Eq. 2 scaled, the move rule and, for
+// refinement, the target's own vertex still in place.
+template <bool REFINE>
+__device__ __forceinline__ void propose_move(WS &w, const Ctl &ct, int32_t i, int32_t d, i128 bsc, int32_t bc,
+                                             int64_t kid, uint8_t sv, Shared &sm) {
+  if (bc == INT32_MAX) return;
+  const int64_t Ki = w.Kp[i];
+  const i128 S = bsc - (i128)ct.A * kid - (i128)ct.p * Ki * (Ki - w.Sp[d]);
+  bool propose = S > 0;
+  if (REFINE && propose && w.Cp[bc] != bc) propose = false;
+  if (!propose) return;
+  const unsigned slot = atomicAdd(&sm.nprop, 1u);
+  w.pi[slot] = i;
+  w.pc[slot] = bc;
+  w.pS[slot] = S;
+  if (REFINE) w.stamp[i] = sv;
+}
+
 template <bool REFINE, typename WT>
 __device__ void decide(const Lvl<WT> &g, WS &w, const Ctl &ct, int32_t kb, int32_t ke, uint8_t sv,
                        int32_t *skeys_all, u64 *svals_all, Shared &sm) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) { sm.nprop = 0; sm.nlong = 0; sm.nmed = 0; }
+  __syncthreads();
+  // Rows of at most SB_GROUP_ROW entries: groups of 8 lanes, four vertices per
+  // warp, a 64-slot table each.  Longer rows are set aside: up to half the
+  // warp table for the warp pass below, the rest for the block pass.
+  {
+    constexpr int G = 8, GPW = 32 / G, GS = SB_WARP_SLOTS / GPW;
+    const int gw = lane / G, gl = lane % G, leader = gw * G;
+    int32_t *gkeys = skeys_all + warp * SB_WARP_SLOTS + gw * GS;
+    u64 *gvals = svals_all + warp * SB_WARP_SLOTS + gw * GS;
+    for (int32_t kb2 = kb + warp * GPW; kb2 < ke; kb2 += nw * GPW) {  // uniform per warp
+      const int32_t k = kb2 + gw;
+      const bool valid = k < ke;
+      const int32_t i = valid ? w.vl[k] : 0;
+      bool act = false;
+      if (gl == 0 && valid) {
+        if (!REFINE) {
+          act = !w.proc[i];
+          w.proc[i] = 1;
+        } else {
+          act = w.ch[w.CB[i]] && w.Cp[i] == i && w.Sp[i] == w.Kp[i];
+        }
+      }
+      act = __shfl_sync(FULL_MASK, act, leader);
+      int64_t e0 = 0, e1 = 0;
+      if (act) { e0 = g.off[i]; e1 = g.off[i + 1]; }
+      if (act && e1 - e0 > SB_GROUP_ROW) {
+        if (gl == 0) {
+          if (2 * (e1 - e0) > SB_WARP_SLOTS) w.longl[atomicAdd(&sm.nlong, 1u)] = i;
+          else w.cv[atomicAdd(&sm.nmed, 1u)] = i;
+        }
+        act = false;
+      }
+      int lh = 1;
+      if (act) {
+        lh = log2_at_least(2 * (e1 - e0));
+        for (int s2 = gl; s2 < (1 << lh); s2 += G) { gkeys[s2] = LEIDEN_EMPTY_KEY; gvals[s2] = 0; }
+      }
+      __syncwarp();
+      const int32_t d = act ? w.Cp[i] : 0;
+      const int32_t cbi = (REFINE && act) ? w.CB[i] : 0;
+      int64_t span = act ? e1 - e0 : 0;
+      for (int o = 16; o; o >>= 1) {
+        const int64_t y = shfl_xor_i64(span, o);
+        span = y > span ? y : span;
+      }
+      for (int64_t xb = 0; xb < span; xb += G) {  // uniform per warp
+        const int64_t e = e0 + xb + gl;
+        const bool in = act && e < e1;
+        const int32_t j = in ? g.idx[e] : -1;
+        const u64 wv = in ? (u64)(int64_t)g.w[e] : 0;
+        bool ok = in && j != i;
+        if (REFINE && ok && w.CB[j] != cbi) ok = false;
+        const int32_t c = ok ? w.Cp[j] : LEIDEN_EMPTY_KEY;
+        u64 sum = 0;
+        const unsigned long long key = ((unsigned long long)(uint32_t)gw << 32) | (uint32_t)c;
+        if (warp_combine(key, ok, wv, &sum, sm.wscr[warp])) tbl_add(gkeys, gvals, lh, c, sum, &sm.err);
+      }
+      __syncwarp();
+      i128 bsc = 0;
+      int32_t bc = INT32_MAX;
+      int64_t kid = 0;
+      if (act) {
+        const i128 A = (i128)ct.A;
+        const i128 B = (i128)ct.p * (i128)w.Kp[i];
+        for (int s2 = gl; s2 < (1 << lh); s2 += G) {
+          const int32_t c = gkeys[s2];
+          if (c == LEIDEN_EMPTY_KEY) continue;
+          const int64_t v = (int64_t)gvals[s2];
+          if (c == d) { kid = v; continue; }
+          const i128 sc = A * (i128)v - B * (i128)w.Sp[c];
+          if (better128(sc, c, bsc, bc)) { bsc = sc; bc = c; }
+        }
+      }
+      for (int o = G / 2; o; o >>= 1) {
+        const i128 osc = shfl_xor_i128(bsc, o);
+        const int32_t oc = __shfl_xor_sync(FULL_MASK, bc, o);
+        kid += shfl_xor_i64(kid, o);
+        if (better128(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
+      }
+      if (act && gl == 0) propose_move<REFINE>(w, ct, i, d, bsc, bc, kid, sv, sm);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // medium rows: one warp each, a table of up to SB_WARP_SLOTS slots
   int32_t *keys = skeys_all + warp * SB_WARP_SLOTS;
   u64 *vals = svals_all + warp * SB_WARP_SLOTS;
-  if (threadIdx.x == 0) { sm.nprop = 0; sm.nlong = 0; }
-  __syncthreads();
-  for (int32_t k = kb + warp; k < ke; k += nw) {
-    const int32_t i = w.vl[k];
-    bool act = false;
-    if (lane == 0) {
-      if (!REFINE) {
-        act = !w.proc[i];
-        w.proc[i] = 1;
-      } else {
-        act = w.ch[w.CB[i]] && w.Cp[i] == i && w.Sp[i] == w.Kp[i];
-      }
-    }
-    act = __shfl_sync(FULL_MASK, act, 0);
-    if (!act) continue;
+  const unsigned nmed = sm.nmed;
+  for (unsigned t = warp; t < nmed; t += nw) {
+    const int32_t i = w.cv[t];
     const int64_t e0 = g.off[i], e1 = g.off[i + 1];
-    if (2 * (e1 - e0) > SB_WARP_SLOTS) {
-      if (lane == 0) w.longl[atomicAdd(&sm.nlong, 1u)] = i;
-      continue;
-    }
     const int lh = log2_at_least(2 * (e1 - e0));
     for (int s = lane; s < (1 << lh); s += 32) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     __syncwarp();
@@ -264,19 +353,7 @@ __device__ void decide(const Lvl<WT> &g, WS &w, const Ctl &ct, int32_t kb, int32
       kid += shfl_xor_i64(kid, o);
       if (better128(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
     }
-    if (lane == 0 && bc != INT32_MAX) {
-      const int64_t Ki = w.Kp[i];
-      const i128 S = bsc - (i128)ct.A * kid - (i128)ct.p * Ki * (Ki - w.Sp[d]);
-      bool propose = S > 0;
-      if (REFINE && propose && w.Cp[bc] != bc) propose = false;
-      if (propose) {
-        const unsigned slot = atomicAdd(&sm.nprop, 1u);
-        w.pi[slot] = i;
-        w.pc[slot] = bc;
-        w.pS[slot] = S;
-        if (REFINE) w.stamp[i] = sv;
-      }
-    }
+    if (lane == 0) propose_move<REFINE>(w, ct, i, d, bsc, bc, kid, sv, sm);
     __syncwarp();
   }
   __syncthreads();
