@@ -220,6 +220,21 @@ def run_reference(args):
     return 0
 
 
+def combine_ranks(total_ms, static_ms, edges, launches, world, device):
+    """Whole-job figures of independent replicas: the slowest rank's times
+    (max over ranks) and the work of all ranks (sums).  One process per GPU;
+    the reduction runs on the process group's backend (NCCL on the GPUs)."""
+    if world <= 1:
+        return total_ms, static_ms, edges, launches
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, static_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([edges, launches], dtype=torch.float64, device=device)
+    dist.all_reduce(e)
+    return float(t[0]), float(t[1]), float(e[0]), int(e[1])
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -291,16 +306,8 @@ def run_ours(args):
     static_ms = sum(r["static_ms"] for r in rec)
     static_edges = sum(r["static_edges"] for r in rec)
     # max over ranks of the device time
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, static_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([static_edges, launches], device=dev, dtype=torch.float64)
-        dist.all_reduce(e)
-        total_ms, static_ms = float(t[0]), float(t[1])
-        static_edges_all, launches = float(e[0]), int(e[1])  # launches: all ranks
-    else:
-        static_edges_all = static_edges
+    total_ms, static_ms, static_edges_all, launches = combine_ranks(total_ms, static_ms, static_edges, launches,
+                                                                     world, dev)
     value = static_edges_all / (static_ms / 1000.0)
 
     # roofline of the dominant kernel family (local-move decide kernels)
