@@ -172,6 +172,11 @@ typedef struct {
   double t_refine_ms[LEIDEN_STATS_PASSES];
   double t_agg_ms[LEIDEN_STATS_PASSES];
   double t_pass_ms[LEIDEN_STATS_PASSES];
+  /* the same decide-kernel figures for the first pass alone (the first-pass
+   * local-moving phase; in a profiler it is the NVTX range local_move_pass0) */
+  double move0_kernel_ms;
+  int64_t move0_kernel_launches;
+  double move0_bytes;
 } leiden_run_stats;
 
 /* Copies the statistics of the last run into *out (HOST). */

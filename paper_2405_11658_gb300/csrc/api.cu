@@ -391,7 +391,12 @@ int local_move(Run &r, GraphView<WT> g, const Buckets &b, bool first_pass, doubl
   const int64_t cand = (int64_t)c->h_ctr[CTR_CANDIDATES];
   c->stats.move_scanned_entries += ent;
   c->stats.move_scanned_vertices += ver;
-  c->stats.move_bytes += (double)ent * (8.0 + sizeof(WT)) + (double)ver * 42.0 + (double)cand * 8.0;
+  const double bytes = (double)ent * (8.0 + sizeof(WT)) + (double)ver * 42.0 + (double)cand * 8.0;
+  c->stats.move_bytes += bytes;
+  if (first_pass) {
+    c->stats.move0_bytes += bytes;
+    c->stats.move0_kernel_launches = c->stats.move_kernel_launches;  // the first pass's launches come first
+  }
   return li;
 }
 
@@ -462,7 +467,7 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
   int64_t moves = 0, rmoves = 0;
   int li;
   {
-    Phase ph("local_move");
+    Phase ph(lp == 0 ? "local_move_pass0" : "local_move");
     li = local_move<WT, ST>(r, g, b, lp == 0, tau, &moves);
   }
   if (li < 0) return li;
@@ -642,13 +647,15 @@ int fail_run(leiden_ctx *c, int rc) {
 
 void finish_timing(leiden_ctx *c) {
   if (!c->timing) return;
-  double ms = 0;
+  double ms = 0, ms0 = 0;
   for (int64_t k = 0; k < c->stats.move_kernel_launches; k++) {
     float t = 0;
     cudaEventElapsedTime(&t, c->evs[2 * k], c->evs[2 * k + 1]);
     ms += t;
+    if (k < c->stats.move0_kernel_launches) ms0 += t;
   }
   c->stats.move_kernel_ms = ms;
+  c->stats.move0_kernel_ms = ms0;
 }
 
 }  // namespace
