@@ -365,7 +365,9 @@ typedef struct {
 } leiden_request_info;
 
 /* Waits up to timeout_ms (< 0: forever) for a request; LEIDEN_ETIMEOUT if it
- * is not done by then.  *out (HOST) receives its record. */
+ * is not done by then.  *out (HOST) receives its record, after which the
+ * request is forgotten: each request is waited on once (a second wait gets
+ * LEIDEN_EINVAL). */
 int leiden_server_wait(leiden_server *s, int64_t request_id, double timeout_ms, leiden_request_info *out);
 
 /* Copies a graph's current membership (n labels) into host_out, after

@@ -625,14 +625,24 @@ Resident *idle_graph(leiden_server *s, std::unique_lock<std::mutex> &lk, int32_t
 
 extern "C" int leiden_server_membership(leiden_server *s, int32_t graph_id, int32_t *host_out, int64_t n) {
   if (!s || (n > 0 && !host_out)) return LEIDEN_EINVAL;
-  std::unique_lock<std::mutex> lk(s->mu);
-  Resident *g = idle_graph(s, lk, graph_id);
-  if (!g || n != g->n) return LEIDEN_EINVAL;
-  if (n > 0 && cudaMemcpy(host_out, g->C[g->mem], (size_t)n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
-    cudaGetLastError();
-    return LEIDEN_ECUDA;
+  Resident *g = nullptr;
+  const int32_t *src = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    g = idle_graph(s, lk, graph_id);
+    if (!g || n != g->n) return LEIDEN_EINVAL;
+    g->busy = true;  // no worker touches the graph while it is copied out
+    src = g->C[g->mem];
   }
-  return LEIDEN_OK;
+  int rc = LEIDEN_OK;
+  if (n > 0 && cudaMemcpy(host_out, src, (size_t)n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    rc = LEIDEN_ECUDA;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  g->busy = false;
+  s->cv.notify_all();
+  return rc;
 }
 
 extern "C" int leiden_server_evict(leiden_server *s, int32_t graph_id) {

@@ -108,6 +108,28 @@ def test_static_full_run_properties(work):
     assert all(a >= b for a, b in zip(st["nv"], st["nv"][1:]))
 
 
+@pytest.mark.parametrize("mode", ["ND", "DS"])
+def test_nd_ds_first_pass_bit_exact_at_full_size(work, mode):
+    g, gt, dels, ins, ctx = work
+    off, idx, w = g
+    G0 = L.Graph.from_numpy(*g)
+    prior, _ = ctx.static(G0, L.Opts(max_passes=1))
+    prior = prior.cpu().numpy()
+    K = rowsum(off, w)
+    sig = np.bincount(prior, weights=K.astype(np.float64), minlength=len(K)).astype(np.int64)
+    ref = O.update(*gt, prior, K, sig, dels, ins, mode, O.LeidenOpts(max_passes=1))
+    Gt = L.Graph.from_numpy(*gt)
+    dev = Gt.off.device
+    memb, Kt, St, q = ctx.update(Gt, torch.from_numpy(prior).to(dev), L.Edges.from_numpy(dels),
+                                 L.Edges.from_numpy(ins), mode, opts=L.Opts(max_passes=1),
+                                 prior_K=torch.from_numpy(K).to(dev), prior_Sigma=torch.from_numpy(sig).to(dev))
+    assert np.array_equal(memb.cpu().numpy(), ref.membership)
+    assert np.array_equal(St.cpu().numpy(), ref.Sigma)
+    assert q == ref.q
+    st = ctx.stats()
+    assert st["affected0"] == ref.stats["affected0"] and st["changed0"] == ref.stats["changed0"]
+
+
 def test_df_update_at_full_size(work):
     g, gt, dels, ins, ctx = work
     off, idx, w = g
