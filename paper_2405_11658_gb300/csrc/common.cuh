@@ -12,6 +12,16 @@ typedef unsigned long long u64;
 
 namespace lk {
 
+// Value type of the decide kernels' hashtables.  The 64-bit score path is
+// taken only when 4 (2m)^2 max(p, q) < 2^62, so 2m < 2^31 and every summed
+// K_{i->c} (at most K_i <= 2m) fits 32 bits: those tables hold 8-byte slots
+// instead of 12.
+template <typename ST> struct TableVal { typedef u64 type; };
+template <> struct TableVal<int64_t> { typedef uint32_t type; };
+
+__device__ __forceinline__ void add_val(u64 *p, u64 w) { atomicAdd(p, w); }
+__device__ __forceinline__ void add_val(uint32_t *p, u64 w) { atomicAdd((unsigned *)p, (unsigned)w); }
+
 // Multiplicative hash of a community ID; the top bits index the table.
 __device__ __forceinline__ uint32_t hash32(int32_t c) {
   return (uint32_t)c * 0x9E3779B1u;

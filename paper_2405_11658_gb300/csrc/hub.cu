@@ -53,8 +53,9 @@ __global__ void __launch_bounds__(1024) hub_prep_k(MoveArgs<WT> a, bool refine, 
       if (hub_eligible(a, i, refine)) {
         const int64_t deg = a.g.off[i + 1] - a.g.off[i];
         const int64_t cap = deg < a.g.n ? deg : a.g.n;
-        int64_t t = HUB_SCAN_CHUNK;
-        while (t < 2 * cap) t <<= 1;
+        // at least twice the distinct keys, in whole scan chunks (the home
+        // slot comes from a multiply-shift, so any size works)
+        const int64_t t = ((2 * cap + HUB_SCAN_CHUNK - 1) / HUB_SCAN_CHUNK) * HUB_SCAN_CHUNK;
         v[0] = t;
         v[1] = (deg + HUB_CHUNK - 1) / HUB_CHUNK;
         v[2] = t / HUB_SCAN_CHUNK;
@@ -106,28 +107,23 @@ __device__ __forceinline__ int64_t find_item(const int64_t *offs, int64_t n, int
   return lo;
 }
 
-__device__ __forceinline__ void hub_table_add(int32_t *keys, u64 *vals, uint64_t mask, int sh, int32_t c, u64 w,
-                                              u64 *err) {
-  uint64_t s = (uint64_t)(hash32(c) >> sh);
-  for (uint64_t probe = 0; probe <= mask; probe++) {
+template <typename VT>
+__device__ __forceinline__ void hub_table_add(int32_t *keys, VT *vals, uint64_t t, int32_t c, u64 w, u64 *err) {
+  uint64_t s = ((uint64_t)hash32(c) * t) >> 32;
+  for (uint64_t probe = 0; probe < t; probe++) {
     const int32_t k = *(volatile int32_t *)&keys[s];
-    if (k == c) { atomicAdd(&vals[s], w); return; }
+    if (k == c) { add_val(&vals[s], w); return; }
     if (k == LEIDEN_EMPTY_KEY) {
       const int32_t old = atomicCAS(&keys[s], LEIDEN_EMPTY_KEY, c);
-      if (old == LEIDEN_EMPTY_KEY || old == c) { atomicAdd(&vals[s], w); return; }
+      if (old == LEIDEN_EMPTY_KEY || old == c) { add_val(&vals[s], w); return; }
     }
-    s = (s + 1) & mask;
+    s = s + 1 == t ? 0 : s + 1;
   }
   atomicOr(err, 16ull);
 }
 
-__device__ __forceinline__ int log2_exact(int64_t t) {
-  int k = 0;
-  while (((int64_t)1 << k) < t) k++;
-  return k;
-}
 
-template <typename WT>
+template <typename WT, typename VT>
 __global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine, HubWork hw) {
   __shared__ u64 wscratch[8][32];
   const int64_t nitems = hw.tot[1];
@@ -138,9 +134,8 @@ __global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine,
     const int64_t c0 = e0 + (w - hw.ioff[k]) * HUB_CHUNK;
     const int64_t c1 = c0 + HUB_CHUNK < e1 ? c0 + HUB_CHUNK : e1;
     const int64_t t = hw.tsz[k];
-    const int lh = log2_exact(t);
     int32_t *keys = a.gkeys + hw.toff[k];
-    u64 *vals = a.gvals + hw.toff[k];
+    VT *vals = reinterpret_cast<VT *>(a.gvals) + hw.toff[k];
     const int32_t cbi = refine ? a.CB[i] : 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t cb = c0 + 32 * warp; cb < c1; cb += blockDim.x) {  // warp-uniform chunks
@@ -156,7 +151,7 @@ __global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine,
       }
       u64 sum = 0;
       if (warp_combine((unsigned long long)(uint32_t)c, c != LEIDEN_EMPTY_KEY, wv, &sum, wscratch[warp]))
-        hub_table_add(keys, vals, (uint64_t)(t - 1), 32 - lh, c, sum, &a.ctr[CTR_ERROR]);
+        hub_table_add(keys, vals, (uint64_t)t, c, sum, &a.ctr[CTR_ERROR]);
     }
   }
 }
@@ -182,7 +177,7 @@ __global__ void __launch_bounds__(256) hub_scan_k(MoveArgs<WT> a, HubWork hw) {
     const ST B = (ST)a.p * (ST)a.K[i];
     const int64_t s0 = (w - hw.soff[k]) * HUB_SCAN_CHUNK;
     int32_t *keys = a.gkeys + hw.toff[k];
-    u64 *vals = a.gvals + hw.toff[k];
+    typename TableVal<ST>::type *vals = reinterpret_cast<typename TableVal<ST>::type *>(a.gvals) + hw.toff[k];
     ST bsc = 0;
     int32_t bc = INT32_MAX;
     int64_t kid = 0, cand = 0;
@@ -316,7 +311,7 @@ template <typename WT, typename ST, bool REFINE, bool ASYNC>
 void launch_hubs(const MoveArgs<WT> &a, const HubWork &hw, int sms, cudaStream_t s) {
   if (a.list_n <= 0) return;
   LK_COUNTED hub_prep_k<WT><<<1, 1024, 0, s>>>(a, REFINE, hw);
-  LK_COUNTED hub_insert_k<WT><<<sms * 8, 256, 0, s>>>(a, REFINE, hw);
+  LK_COUNTED hub_insert_k<WT, typename TableVal<ST>::type><<<sms * 8, 256, 0, s>>>(a, REFINE, hw);
   LK_COUNTED hub_scan_k<WT, ST><<<sms * 8, 256, 0, s>>>(a, hw);
   LK_COUNTED hub_final_k<WT, ST, REFINE, ASYNC><<<(unsigned)((a.list_n + 255) / 256), 256, 0, s>>>(a, hw);
 }

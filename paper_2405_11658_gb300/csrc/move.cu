@@ -20,16 +20,6 @@
 
 namespace lk {
 
-// Value type of the shared-memory tables.  The 64-bit score path is taken only
-// when 4 (2m)^2 max(p, q) < 2^62, so 2m < 2^31 and every summed K_{i->c}
-// (at most K_i <= 2m) fits 32 bits: those tables hold 8-byte slots instead
-// of 12, and more warps fit on an SM.
-template <typename ST> struct TableVal { typedef u64 type; };
-template <> struct TableVal<int64_t> { typedef uint32_t type; };
-
-__device__ __forceinline__ void add_val(u64 *p, u64 w) { atomicAdd(p, w); }
-__device__ __forceinline__ void add_val(uint32_t *p, u64 w) { atomicAdd((unsigned *)p, (unsigned)w); }
-
 template <typename ST>
 __device__ __forceinline__ bool better(ST sc, int32_t c, ST bsc, int32_t bc) {
   return c != INT32_MAX && (bc == INT32_MAX || sc > bsc || (sc == bsc && c < bc));
