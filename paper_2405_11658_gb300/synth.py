@@ -40,14 +40,28 @@ def edges_to_csr(n: int, u, v, w=None):
     u, v, w = u[keep], v[keep], w[keep]
     a, b = np.minimum(u, v), np.maximum(u, v)
     key = a * n + b
-    key, first = np.unique(key, return_index=True)
-    w = w[first]
+    if len(w) == 0 or np.all(w == w[0]):
+        # every duplicate has the same weight: a plain sort deduplicates
+        key = np.sort(key)
+        if len(key):
+            key = key[np.concatenate([[True], key[1:] != key[:-1]])]
+        w = np.full(len(key), w[0] if len(w) else 1, np.int64)
+    else:
+        key, first = np.unique(key, return_index=True)
+        w = w[first]
     a, b = key // n, key % n
     src = np.concatenate([a, b])
     dst = np.concatenate([b, a])
     wt = np.concatenate([w, w])
-    order = np.argsort(src * n + dst, kind="stable")
-    src, dst, wt = src[order], dst[order], wt[order]
+    ekey = src * n + dst                      # distinct: one per CSR entry
+    if len(wt) and wt.min() >= 0 and wt.max() < 8 and n <= (1 << 30):
+        # small weights travel in the low bits of the sort key
+        packed = np.sort((ekey << 3) | wt)
+        ekey, wt = packed >> 3, packed & 7
+        src, dst = ekey // n, ekey % n
+    else:
+        order = np.argsort(ekey, kind="stable")
+        src, dst, wt = src[order], dst[order], wt[order]
     off = np.zeros(n + 1, np.int64)
     off[1:] = np.cumsum(np.bincount(src, minlength=n))
     return off, dst.astype(np.int32), wt.astype(np.int32)

@@ -1,0 +1,67 @@
+"""The seeded input generators: the CSR builder against a plain dictionary
+construction, and the shape of each generated graph (symmetric, sorted rows,
+no self-loops or duplicate entries, positive weights)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_2405_11658_gb300 import synth as S
+
+
+def dict_csr(n, u, v, w):
+    """First weight seen per undirected pair, self-loops dropped, both
+    directions, rows sorted by neighbour."""
+    first = {}
+    for a, b, x in zip(u, v, w):
+        if a != b:
+            first.setdefault((min(a, b), max(a, b)), x)
+    rows = [[] for _ in range(n)]
+    for (a, b), x in first.items():
+        rows[a].append((b, x))
+        rows[b].append((a, x))
+    off = np.zeros(n + 1, np.int64)
+    idx, wt = [], []
+    for i in range(n):
+        for j, x in sorted(rows[i]):
+            idx.append(j)
+            wt.append(x)
+        off[i + 1] = len(idx)
+    return off, np.asarray(idx, np.int32), np.asarray(wt, np.int32)
+
+
+@pytest.mark.parametrize("wkind", ["none", "equal", "small", "large"])
+@pytest.mark.parametrize("seed", range(4))
+def test_edges_to_csr_matches_a_dictionary_construction(wkind, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 40))
+    m = int(rng.integers(0, 200))
+    u = rng.integers(0, n, m)
+    v = rng.integers(0, n, m)
+    w = {"none": None, "equal": np.full(m, 3), "small": rng.integers(1, 5, m),
+         "large": rng.integers(1, 1000, m)}[wkind]
+    got = S.edges_to_csr(n, u, v, w)
+    want = dict_csr(n, u.tolist(), v.tolist(), [1] * m if w is None else w.tolist())
+    for a, b in zip(got, want):
+        assert a.dtype == b.dtype and np.array_equal(a, b)
+
+
+def valid_csr(off, idx, w):
+    n = len(off) - 1
+    assert off[0] == 0 and np.all(np.diff(off) >= 0) and off[-1] == len(idx) == len(w)
+    rows = np.repeat(np.arange(n), np.diff(off))
+    assert np.all(rows != idx) and np.all(w > 0)
+    key = rows * n + idx
+    assert np.all(np.diff(key) > 0)                      # sorted rows, no duplicates
+    rkey = idx.astype(np.int64) * n + rows               # the transpose holds the same entries
+    order = np.argsort(rkey)
+    assert np.array_equal(rkey[order], key) and np.array_equal(w[order], w)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: S.planted_partition(500, 5, 0.05, 0.002, 1), lambda: S.rmat(10, 8, seed=2),
+    lambda: S.chung_lu(2000, 8000, 2.1, 1, 4, seed=3), lambda: S.grid(30, 0.05, 0.01, seed=4),
+    lambda: S.kmer(3000, 64, 2.1, seed=5), lambda: S.erdos_renyi(60, 0.1, 6, wmax=9),
+    lambda: S.ring_of_cliques(6, 4)])
+def test_generated_graphs_are_valid_symmetric_csr(make):
+    valid_csr(*make())
