@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--sched", default="det", choices=["det", "async"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "serving"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "serving", "lowdeg"])
     ap.add_argument("--profile-static", action="store_true",
                     help="run one Static Leiden on the workload graph and print its statistics (for profilers)")
+    ap.add_argument("--lowdeg-samples", type=int, default=3, help="batches per size on the low-degree graphs")
     ap.add_argument("--serving-graphs", type=int, default=64)
     ap.add_argument("--serving-max-n", type=float, default=1e7)
     ap.add_argument("--serving-per-graph", type=int, default=10)
@@ -555,6 +556,122 @@ def run_serving(args):
     print(json.dumps(line))
     return 0
 
+LOWDEG_FRACS = (1e-6, 1e-5, 1e-4, 1e-3)
+
+
+def _lowdeg_graph(job):
+    """One low-degree graph at full size and its batches: (name, graph,
+    [(frac, dels, ins), ...]), samples batches per size."""
+    name, samples = job
+    from paper_2405_11658_gb300 import synth as S
+    if name == "grid":
+        g = S.grid(5000, 0.05, 0.001, seed=0x1EDE0 + 3)
+    else:
+        g = S.kmer(100_000_000, 64.0, 2.1, seed=0x1EDE0 + 4)
+    pairs = S.undirected_pairs(*g)
+    nedges = len(pairs[0])
+    batches = []
+    for i, frac in enumerate(LOWDEG_FRACS):
+        for k in range(samples):
+            size = max(2, int(round(frac * nedges)))
+            batches.append((frac, *S.random_batch(*g, size, seed=2000 + 10 * i + k, pairs=pairs)))
+    return name, g, batches
+
+
+def run_lowdeg(args):
+    """Static, DS and DF Leiden on the two low-degree graphs at full size
+    (5000 x 5000 grid with 5% of edges removed and 0.1% |V| shortcuts;
+    1e8-vertex k-mer-like paths with mean degree 2.1), batches of 1e-6 ..
+    1e-3 |E|; prints one JSON line."""
+    import multiprocessing as mp
+    jobs = [("kmer", args.lowdeg_samples), ("grid", args.lowdeg_samples)]
+    with mp.get_context("spawn").Pool(2) as pool:
+        work = pool.map(_lowdeg_graph, jobs, chunksize=1)
+    import torch
+    import paper_2405_11658_gb300 as L
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    opts = L.Opts(sched=L.DET if args.sched == "det" else L.ASYNC)
+    out, tot_edges, tot_ms = {}, 0, 0.0
+    peak, peak_kind = peaks()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        b.synchronize()
+        return r, a.elapsed_time(b)
+
+    launches0 = L.kernel_launches()
+    with Clocks(0) as clk:
+        for name, g, batches in sorted(work):
+            off, idx, w = g
+            n, nnz = len(off) - 1, len(idx)
+            max_nnz = nnz + 2 * max(len(b[2][0]) for b in batches) + 16
+            G0 = L.Graph.from_numpy(off, idx, w, device=dev)
+            with L.Context(max_n=n, max_nnz=max_nnz, stream=stream) as ctx:
+                for _ in range(args.warmup):
+                    Cs, _ = ctx.static(G0, opts, want_q=False)
+                st_ms, st_edges, mv = [], [], []
+                for _ in range(args.steps):
+                    ctx.set_timing(True)
+                    (Cs, _), ms = timed(lambda: ctx.static(G0, opts, want_q=False))
+                    ctx.set_timing(False)
+                    st = ctx.stats()
+                    st_ms.append(ms)
+                    st_edges.append(sum(st["nnz"][:st["passes"]]))
+                    mv.append((st["move0_bytes"], st["move0_kernel_ms"], st["move0_kernel_launches"]))
+                C0, K0, S0, _ = ctx.update(G0, Cs, None, None, "ND", opts, want_q=False)
+                per = {}
+                for frac, dels, ins in batches:
+                    dE, iE = L.Edges.from_numpy(dels, device=dev), L.Edges.from_numpy(ins, device=dev)
+                    Gt, t_apply = timed(lambda: ctx.apply_batch(G0, dE, iE, cap_nnz=max_nnz))
+                    rec = per.setdefault(f"{frac:g}", {"apply": [], "DS": [], "DF": [], "static": [], "affected": []})
+                    rec["apply"].append(t_apply)
+                    for mode in ("DS", "DF"):
+                        _, t = timed(lambda: ctx.update(Gt, C0, dE, iE, mode, opts, prior_K=K0, prior_Sigma=S0,
+                                                        want_q=False))
+                        rec[mode].append(t)
+                        if mode == "DF":
+                            rec["affected"].append(ctx.stats()["affected0"])
+                    _, t = timed(lambda: ctx.static(Gt, opts, want_q=False))
+                    rec["static"].append(t)
+                    del Gt
+                res = {}
+                for key, rec in per.items():
+                    s50 = float(np.median(rec["static"]))
+                    res[key] = {"apply_ms_p50": float(np.median(rec["apply"])), "static_ms_p50": s50,
+                                "df_affected0_p50": int(np.median(rec["affected"])), "samples": len(rec["DF"])}
+                    for mode in ("DS", "DF"):
+                        res[key][f"{mode.lower()}_ms_p50"] = float(np.percentile(rec[mode], 50))
+                        res[key][f"{mode.lower()}_ms_p99"] = float(np.percentile(rec[mode], 99))
+                        res[key][f"{mode.lower()}_speedup_vs_static"] = s50 / float(np.median(rec[mode]))
+                b, ms, nl = (sum(x[i] for x in mv) for i in range(3))
+                ach = (b / nl) / ((ms / nl) / 1000.0) / 1e9 if ms > 0 else None
+                out[name] = {"vertices": n, "csr_entries": nnz, "static_ms_mean": float(np.mean(st_ms)),
+                             "static_edges_per_s": sum(st_edges) / (sum(st_ms) / 1000.0),
+                             "static_passes": st["passes"], "static_iters": st["iters"],
+                             "first_pass_decide": {"achieved_gbs": ach, "frac": (ach / peak) if ach else None,
+                                                   "ms_per_launch": ms / max(1, nl), "launches": nl},
+                             "batches": res}
+                tot_edges += sum(st_edges)
+                tot_ms += sum(st_ms)
+    launches = L.kernel_launches() - launches0
+    line = {"metric": METRIC, "value": tot_edges / (tot_ms / 1000.0), "unit": "edges/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / max(1, 2 * args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "low-degree: 5000x5000 grid (5% edges removed, 0.1%|V| shortcuts) and "
+                                   "1e8-vertex k-mer-like paths (mean 64, degree 2.1); Static, DS, DF",
+                       "batch_fracs": list(LOWDEG_FRACS), "samples_per_size": args.lowdeg_samples,
+                       "schedule": args.sched, "l2": "inputs larger than L2 (CSR 0.8 and 1.7 GB), no flush",
+                       "peak_gbs": peak, "peak_kind": peak_kind},
+            "graphs": out, "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
 
 def run_profile_static(args):
     """One Static Leiden (DET) on the benchmark graph with the decide kernels
@@ -591,6 +708,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "lowdeg":
+        return run_lowdeg(args)
     return run_ours(args)
 
 

@@ -27,10 +27,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-import scipy.sparse as sp  # noqa: E402
-from scipy.sparse.csgraph import connected_components  # noqa: E402
-
 import paper_2405_11658_gb300 as L  # noqa: E402
+from tests.props import check_properties, rowsum  # noqa: E402
 
 SCALE, EF = 22, 16
 SEED = 0x1EDE0 + 1
@@ -47,42 +45,6 @@ def work():
     max_nnz = max(len(idx), len(gt[1])) + 16
     with L.Context(max_n=len(off) - 1, max_nnz=max_nnz) as ctx:
         yield g, gt, dels, ins, ctx
-
-
-def rowsum(off, w):
-    n = len(off) - 1
-    rows = np.repeat(np.arange(n), np.diff(off))
-    # float64 sums of integers far below 2^53 are exact
-    return np.bincount(rows, weights=np.asarray(w, np.float64), minlength=n).astype(np.int64)
-
-
-def check_properties(off, idx, w, memb, q, Sigma=None):
-    n = len(off) - 1
-    memb = np.asarray(memb, np.int64)
-    # canonical labels: community IDs appear in increasing order of their
-    # smallest member, densely numbered from 0
-    first = np.full(memb.max() + 1, n, np.int64)
-    np.minimum.at(first, memb, np.arange(n))
-    assert np.all(np.diff(first) > 0) and first[0] == 0
-    # Eq. 1 with exact integers (gamma = 1)
-    rows = np.repeat(np.arange(n), np.diff(off))
-    inside = int(np.asarray(w, np.int64)[memb[rows] == memb[idx]].sum())
-    K = rowsum(off, w)
-    sig = np.bincount(memb, weights=K.astype(np.float64), minlength=memb.max() + 1).astype(np.int64)
-    two_m = int(K.sum())
-    assert two_m * two_m < 2**62  # the int64 sum of squares below is exact
-    sq = int((sig * sig).sum())
-    assert q == float(two_m * inside - sq) / (float(two_m) * float(two_m) * 1.0)
-    if Sigma is not None:
-        expect = np.zeros(n, np.int64)
-        expect[:len(sig)] = sig
-        assert np.array_equal(np.asarray(Sigma), expect)
-    # every community is connected: the graph restricted to intra-community
-    # edges has exactly one component per community
-    keep = memb[rows] == memb[idx]
-    A = sp.csr_matrix((np.ones(int(keep.sum()), np.int8), (rows[keep], idx[keep])), shape=(n, n))
-    ncomp, _ = connected_components(A, directed=False)
-    assert ncomp == memb.max() + 1
 
 
 def test_static_first_pass_bit_exact_at_full_size(work):
