@@ -123,6 +123,12 @@ static constexpr int64_t HUB_TABLE_MIN = 4096;
 #ifndef LK_ROW_UNROLL
 #define LK_ROW_UNROLL 1
 #endif
+// Resident blocks per SM the group-tier decide kernels are compiled for (a
+// register cap for 256-thread blocks); 0 leaves the register count to the
+// compiler.
+#ifndef LK_GROUP_MINB
+#define LK_GROUP_MINB 0
+#endif
 
 
 enum {

@@ -127,8 +127,13 @@ __device__ __forceinline__ bool commit_async(const MoveArgs<WT> &a, int32_t i, i
 // ---------------------------------------------------------------------------
 // Group tier: G lanes and 2^LOG2H shared slots per vertex.
 // ---------------------------------------------------------------------------
+#if LK_GROUP_MINB > 0
+#define LK_GROUP_BOUNDS __launch_bounds__(256, LK_GROUP_MINB)
+#else
+#define LK_GROUP_BOUNDS
+#endif
 template <int G, int LOG2H, bool REFINE, bool ASYNC, typename WT, typename ST>
-__global__ void decide_group(MoveArgs<WT> a) {
+__global__ void LK_GROUP_BOUNDS decide_group(MoveArgs<WT> a) {
   constexpr int H = 1 << LOG2H;
   constexpr int GPW = 32 / G;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -150,7 +155,14 @@ __global__ void decide_group(MoveArgs<WT> a) {
   for (int64_t wb = wglob * GPW; wb < a.list_n; wb += nw * GPW) {
     const int64_t li = wb + gw;
     const bool valid = li < a.list_n;
-    int32_t i = valid ? a.list[li] : 0;
+    const int32_t i = valid ? a.list[li] : 0;
+    // The row bounds, C'[i], K'[i] and (DET, a read-only snapshot) Sigma'[d]
+    // do not depend on the eligibility test: they are loaded alongside it, so
+    // a vertex waits for one round of loads here instead of a chain of them.
+    const int64_t h0 = a.g.off[i], h1 = a.g.off[i + 1];
+    const int32_t hd = a.C[i];
+    const int64_t Ki = a.K[i];
+    const int64_t hSd = ASYNC ? 0 : a.Sig[hd];
     bool act = false;
     if (gl == 0 && valid) act = eligible<REFINE>(a, i);
     act = __shfl_sync(FULL_MASK, act, leader);
@@ -158,8 +170,8 @@ __global__ void decide_group(MoveArgs<WT> a) {
     int64_t e0 = 0, e1 = 0;
     int lh = 1;  // table sized for this row: 2^lh >= 2 * degree, lh <= LOG2H
     if (act) {
-      e0 = a.g.off[i];
-      e1 = a.g.off[i + 1];
+      e0 = h0;
+      e1 = h1;
       while (lh < LOG2H && ((int64_t)1 << lh) < 2 * (e1 - e0)) lh++;
     }
     // the longest row of the warp's groups; every loop below is warp-uniform
@@ -177,7 +189,7 @@ __global__ void decide_group(MoveArgs<WT> a) {
       for (int s = gl; s < (1 << lh); s += G) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     __syncwarp();
     const int32_t cbi = (REFINE && act) ? a.CB[i] : 0;
-    if (act) d = a.C[i];
+    if (act) d = hd;
     ST bsc = 0;
     int32_t bc = INT32_MAX;
     int64_t kid = 0;
@@ -197,7 +209,7 @@ __global__ void decide_group(MoveArgs<WT> a) {
         if (c == d) {
           kid = (int64_t)sum;
         } else {
-          const ST sc = (ST)a.A * (ST)(int64_t)sum - (ST)a.p * (ST)a.K[i] * (ST)a.Sig[c];
+          const ST sc = (ST)a.A * (ST)(int64_t)sum - (ST)a.p * (ST)Ki * (ST)a.Sig[c];
           bsc = sc;
           bc = c;
         }
@@ -236,7 +248,7 @@ __global__ void decide_group(MoveArgs<WT> a) {
       __syncwarp();
       if (act) {
         const ST A = (ST)a.A;
-        const ST B = (ST)a.p * (ST)a.K[i];
+        const ST B = (ST)a.p * (ST)Ki;
         scan_slots<ST, VT>(keys, vals, 1 << lh, gl, G, d, A, B, a.Sig, bsc, bc, kid, ncand);
       }
     }
@@ -251,8 +263,7 @@ __global__ void decide_group(MoveArgs<WT> a) {
     bool propose = false;
     i128 S = 0;
     if (act && gl == 0 && bc != INT32_MAX) {
-      const int64_t Ki = a.K[i];
-      S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - a.Sig[d]);
+      S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - (ASYNC ? a.Sig[d] : hSd));
       propose = S > 0;                                   // strictly better only
       if (REFINE && propose && a.C[bc] != bc) propose = false;  // target's vertex left
     }
@@ -342,7 +353,7 @@ template <bool REFINE, bool ASYNC, typename WT, typename ST>
 __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int32_t s_i, s_d, s_act;
-  __shared__ int64_t s_e0, s_e1;
+  __shared__ int64_t s_e0, s_e1, s_K, s_Sd;
   __shared__ ST r_sc[32];
   __shared__ int32_t r_c[32];
   __shared__ int64_t r_kid[32];
@@ -361,11 +372,16 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
   if (threadIdx.x == 0) s_nused = 0;
   for (int64_t li = blockIdx.x; li < a.list_n; li += gridDim.x) {
     if (threadIdx.x == 0) {
+      // loaded alongside the eligibility test, as in the group tiers
       const int32_t i = a.list[li];
+      const int64_t h0 = a.g.off[i], h1 = a.g.off[i + 1];
+      const int32_t hd = a.C[i];
+      const int64_t hK = a.K[i];
+      const int64_t hSd = ASYNC ? 0 : a.Sig[hd];
       const bool act = eligible<REFINE>(a, i);
       s_i = i;
       s_act = act;
-      if (act) { s_d = a.C[i]; s_e0 = a.g.off[i]; s_e1 = a.g.off[i + 1]; }
+      if (act) { s_d = hd; s_e0 = h0; s_e1 = h1; s_K = hK; s_Sd = hSd; }
     }
     __syncthreads();
     if (!s_act) { __syncthreads(); continue; }
@@ -411,7 +427,8 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
     __syncthreads();
     const unsigned nused = s_nused;
     const ST A = (ST)a.A;
-    const ST B = (ST)a.p * (ST)a.K[i];
+    const int64_t Ki = s_K;
+    const ST B = (ST)a.p * (ST)Ki;
     ST bsc = 0;
     int32_t bc = INT32_MAX;
     int64_t kid = 0;
@@ -444,8 +461,7 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
       bool propose = false;
       i128 S = 0;
       if (bc != INT32_MAX) {
-        const int64_t Ki = a.K[i];
-        S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - a.Sig[d]);
+        S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - (ASYNC ? a.Sig[d] : s_Sd));
         propose = S > 0;
         if (REFINE && propose && a.C[bc] != bc) propose = false;
       }
