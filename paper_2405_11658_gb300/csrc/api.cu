@@ -343,6 +343,9 @@ int local_move(Run &r, GraphView<WT> g, const Buckets &b, bool first_pass, doubl
   cudaMemsetAsync(&c->ctr[CTR_MOVES], 0, sizeof(u64), c->st);
   cudaMemsetAsync(&c->ctr[CTR_SCANNED_ENTRIES], 0, 3 * sizeof(u64), c->st);
   while (li < r.o->max_iters) {
+    // every vertex is unprocessed in the first iteration of a pass, except in
+    // the first pass of an update (its affected set only)
+    a.spec = (li == 0 && !(r.dynamic && first_pass)) ? 1 : 0;
     cudaMemsetAsync(&c->ctr[CTR_SUMS_LO], 0, 2 * sizeof(u64), c->st);
     const bool long_rows = b.maxdeg > BIG_ROW;
     for (int s = 0; s < nsub; s++) {
@@ -402,11 +405,12 @@ int local_move(Run &r, GraphView<WT> g, const Buckets &b, bool first_pass, doubl
 
 // Alg. leidenre: one sweep (DET: one sub-sweep per colour class).
 template <typename WT, typename ST>
-int refine(Run &r, GraphView<WT> g, const Buckets &b, int64_t *moves_out) {
+int refine(Run &r, GraphView<WT> g, const Buckets &b, bool all_changed, int64_t *moves_out) {
   leiden_ctx *c = r.c;
   const bool async = r.o->sched == LEIDEN_ASYNC;
   const int nsub = 1 << r.log2S;
   MoveArgs<WT> a = base_args(r, g);
+  a.spec = all_changed ? 1 : 0;  // every vertex starts isolated in a changed bound
   cudaMemsetAsync(&c->ctr[CTR_MOVES], 0, sizeof(u64), c->st);
   if (!async) cudaMemsetAsync(c->stamp, 0, (size_t)(g.n > 0 ? g.n : 1), c->st);
   for (int s = 0; s < nsub; s++) {
@@ -482,7 +486,7 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
   launch_break(nv, c->Cp, c->Kp, c->Sp, c->ch, c->st);
   {
     Phase ph("refine");
-    rc = refine<WT, ST>(r, g, b, &rmoves);
+    rc = refine<WT, ST>(r, g, b, !(r.dynamic && lp == 0), &rmoves);
   }
   if (rc) return rc;
   if (rec) c->stats.t_refine_ms[lp] = ms_since(t_ref);

@@ -72,6 +72,8 @@ struct MoveArgs {
   uint8_t *stamp;        // refinement: sub-sweep in which a vertex proposed
   uint8_t stamp_val;
   int dynamic;           // mark changed communities on migration
+  int spec;              // most listed vertices are eligible: load their headers
+                         // alongside the eligibility test, not after it
   int32_t *prop_i;       // DET proposals
   int32_t *prop_c;
   i128 *prop_S;

@@ -157,15 +157,28 @@ __global__ void LK_GROUP_BOUNDS decide_group(MoveArgs<WT> a) {
     const bool valid = li < a.list_n;
     const int32_t i = valid ? a.list[li] : 0;
     // The row bounds, C'[i], K'[i] and (DET, a read-only snapshot) Sigma'[d]
-    // do not depend on the eligibility test: they are loaded alongside it, so
-    // a vertex waits for one round of loads here instead of a chain of them.
-    const int64_t h0 = a.g.off[i], h1 = a.g.off[i + 1];
-    const int32_t hd = a.C[i];
-    const int64_t Ki = a.K[i];
-    const int64_t hSd = ASYNC ? 0 : a.Sig[hd];
+    // do not depend on the eligibility test.  Where most listed vertices are
+    // eligible they are loaded alongside it (one round of loads instead of a
+    // chain); elsewhere only for the vertices that pass it.
+    int64_t h0 = 0, h1 = 0, Ki = 0, hSd = 0;
+    int32_t hd = 0;
+    if (a.spec) {
+      h0 = a.g.off[i];
+      h1 = a.g.off[i + 1];
+      hd = a.C[i];
+      Ki = a.K[i];
+      if (!ASYNC) hSd = a.Sig[hd];
+    }
     bool act = false;
     if (gl == 0 && valid) act = eligible<REFINE>(a, i);
     act = __shfl_sync(FULL_MASK, act, leader);
+    if (!a.spec && act) {
+      h0 = a.g.off[i];
+      h1 = a.g.off[i + 1];
+      hd = a.C[i];
+      Ki = a.K[i];
+      if (!ASYNC) hSd = a.Sig[hd];
+    }
     int32_t d = 0;
     int64_t e0 = 0, e1 = 0;
     int lh = 1;  // table sized for this row: 2^lh >= 2 * degree, lh <= LOG2H
@@ -372,13 +385,25 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
   if (threadIdx.x == 0) s_nused = 0;
   for (int64_t li = blockIdx.x; li < a.list_n; li += gridDim.x) {
     if (threadIdx.x == 0) {
-      // loaded alongside the eligibility test, as in the group tiers
+      // header loads as in the group tiers
       const int32_t i = a.list[li];
-      const int64_t h0 = a.g.off[i], h1 = a.g.off[i + 1];
-      const int32_t hd = a.C[i];
-      const int64_t hK = a.K[i];
-      const int64_t hSd = ASYNC ? 0 : a.Sig[hd];
+      int64_t h0 = 0, h1 = 0, hK = 0, hSd = 0;
+      int32_t hd = 0;
+      if (a.spec) {
+        h0 = a.g.off[i];
+        h1 = a.g.off[i + 1];
+        hd = a.C[i];
+        hK = a.K[i];
+        if (!ASYNC) hSd = a.Sig[hd];
+      }
       const bool act = eligible<REFINE>(a, i);
+      if (!a.spec && act) {
+        h0 = a.g.off[i];
+        h1 = a.g.off[i + 1];
+        hd = a.C[i];
+        hK = a.K[i];
+        if (!ASYNC) hSd = a.Sig[hd];
+      }
       s_i = i;
       s_act = act;
       if (act) { s_d = hd; s_e0 = h0; s_e1 = h1; s_K = hK; s_Sd = hSd; }
