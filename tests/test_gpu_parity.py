@@ -287,17 +287,16 @@ def test_self_loops_in_input(ctx):
     assert q == ref.q
 
 
-# ASYNC is timing-dependent.  Its modularity stays within 1e-3 of the oracle's
-# schedules on the structured families; on the hub-heavy ones (a few rows of
-# 10^4 entries next to thousands of short rows, weighted Chung-Lu) run-to-run
-# spread reaches a few 1e-3, so the bar there is 1e-2.
-# 1e-3 on graphs with clear community structure.  R-MAT's weak structure
-# leaves many near-equal local optima -- on rmat14 the oracle's own DET and
-# GS schedules end 7e-3 apart -- and in-place commits land in a different one
-# from run to run.  On the hub-dominated graphs a hub's decision is taken over
-# many blocks while other vertices' commits change the state it reads, so a
-# run can end up to about 2e-2 lower (the oracle's schedules themselves differ
-# by 1e-2 on "hubs").
+# ASYNC is timing-dependent: a run may end in a different local optimum than
+# the oracle's schedules, so its modularity is bounded from below, not equated.
+# The bar is 1e-3 on graphs with clear community structure.  R-MAT's weak
+# structure leaves many near-equal local optima -- on rmat14 the oracle's own
+# DET and GS schedules end 7e-3 apart -- and in-place commits land in a
+# different one from run to run (5e-3).  On the hub-dominated graphs (a few
+# rows of 10^4 entries next to thousands of short rows, weighted Chung-Lu) a
+# hub's decision is taken over many blocks while other vertices' commits
+# change the state it reads, so a run can end up to about 1e-2 (Chung-Lu) or
+# 2e-2 ("hubs") lower; the oracle's schedules themselves differ by 1e-2 there.
 ASYNC_TOL = {"pp_1e4": 1e-3, "pp_strong": 1e-3, "grid": 1e-3, "rmat14": 5e-3,
              "chung_lu_w": 1e-2, "hubs": 2e-2}
 
