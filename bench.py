@@ -195,6 +195,22 @@ def cpu_baseline(g, max_passes=1):
             "seconds": round(wall, 3)}
 
 
+def l2_note(csr_bytes):
+    """How the timed steps stand with the 129 MB L2 (no flush between steps)."""
+    if csr_bytes > 129e6:
+        return f"inputs larger than L2 (CSR {csr_bytes / 1e9:.1f} GB), no flush"
+    return f"inputs smaller than L2 (CSR {csr_bytes / 1e6:.0f} MB): L2-warm steps, no flush"
+
+
+def workload_config(scale, n, nnz, sched, world):
+    """The benchmark workload's config object (both arms print the same one)."""
+    return {"workload": f"rmat-s{scale}-ef{EDGE_FACTOR}: batch apply + DF update + Static Leiden",
+            "graph": f"R-MAT scale {scale}, edge factor {EDGE_FACTOR}, a/b/c/d=0.57/0.19/0.19/0.05",
+            "vertices": n, "csr_entries": nnz, "batch_fracs": list(BATCH_FRACS),
+            "schedule": sched, "l2": l2_note(8 * (n + 1) + 8 * nnz),
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -212,8 +228,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
-            "config": {"workload": f"rmat-s{args.scale}-ef{EDGE_FACTOR} static leiden, first pass",
-                       "graph": f"R-MAT scale {args.scale}, edge factor {EDGE_FACTOR}"},
+            "config": workload_config(args.scale, len(g[0]) - 1, len(g[1]), args.sched, world),
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[0]["sample"], "value": v,
                              "unit": "edges/s"},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -376,11 +391,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": f"rmat-s{args.scale}-ef{EDGE_FACTOR}: batch apply + DF update + Static Leiden",
-                       "graph": f"R-MAT scale {args.scale}, edge factor {EDGE_FACTOR}, a/b/c/d=0.57/0.19/0.19/0.05",
-                       "vertices": n, "csr_entries": nnz, "batch_fracs": list(BATCH_FRACS),
-                       "schedule": args.sched, "l2": "inputs larger than L2 (CSR 1.1 GB), no flush",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(args.scale, n, nnz, args.sched, world),
             "static_ms_mean": static_ms / max(1, len(rec)),
             "static_passes": last.get("passes"), "static_iters": last.get("iters"),
             "df": df,
