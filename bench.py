@@ -88,7 +88,8 @@ def peaks():
 # The decide kernels' sources: a DRAM-traffic figure measured by ncu (stored
 # under profiles/) stays valid only while these files are unchanged.
 DECIDE_SOURCES = ("paper_2405_11658_gb300/csrc/move.cu", "paper_2405_11658_gb300/csrc/hub.cu",
-                  "paper_2405_11658_gb300/csrc/internal.h", "paper_2405_11658_gb300/csrc/common.cuh")
+                  "paper_2405_11658_gb300/csrc/internal.h", "paper_2405_11658_gb300/csrc/common.cuh",
+                  "paper_2405_11658_gb300/csrc/api.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "decide_traffic_rmat22.json")
 
 
