@@ -568,3 +568,27 @@ def test_changed_flags_name_the_shared_community():
     assert ch.tolist() == [1, 1, 0, 0]
     ch = O.changed_communities(Cprev, (np.array([1], np.int32), np.array([0], np.int32), one), None)
     assert ch.tolist() == [0, 1, 0, 0]
+
+
+def test_dynamic_modularity_close_to_static_on_average():
+    # Sec. 5.2 reports ND, DS and DF modularity within about 0.002 of Static
+    # on average.  A sanity check over batch sizes and seeds on three graph
+    # families (the average, not every case: dynamic runs start from C^{t-1}
+    # and may end above or below a Static run on the same G^t).
+    gaps = {m: [] for m in ("ND", "DS", "DF")}
+    for g in (S.rmat(11, 16, seed=6), S.grid(50, 0.05, 0.001, seed=7), S.chung_lu(3000, 20000, 2.1, 1, 4, seed=8)):
+        off, idx, w = g
+        n = len(off) - 1
+        st = O.static(*g)
+        K = np.array([w[off[v]:off[v + 1]].sum() for v in range(n)], np.int64)
+        Sg = sigma_of(st.membership, K, n)
+        for frac in (1e-3, 1e-2):
+            for seed in range(2):
+                size = max(2, int(round(frac * len(idx) / 2)))
+                dels, ins = S.random_batch(*g, size, seed=100 + seed)
+                gt = O.apply_batch(*g, dels, ins)
+                q_static = O.static(*gt).q
+                for m in gaps:
+                    gaps[m].append(q_static - O.update(*gt, st.membership, K, Sg, dels, ins, m).q)
+    for m, v in gaps.items():
+        assert np.mean(v) <= 0.002, (m, np.mean(v))
