@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, const in
   uint16_t *used = reinterpret_cast<uint16_t *>(keys + H);
   __shared__ u64 wscratch[16][32];
   __shared__ int64_t s_ws;
-  __shared__ unsigned s_nused, s_wcnt[16];
+  __shared__ unsigned s_nused;
   __shared__ int64_t s_base;
   __shared__ BucketInfo s_b;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
