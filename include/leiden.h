@@ -129,8 +129,10 @@ int leiden_update(leiden_ctx *ctx, const leiden_csr *g_t,
                   double *q_out);
 
 /* Modularity (Eq. 1 at resolution gamma) of membership (DEVICE [n], labels
- * in [0, n)) on g.  q_out is HOST.  Errors: LEIDEN_EINVAL, LEIDEN_ENOMEM,
- * LEIDEN_ECUDA. */
+ * in [0, n)) on g.  q_out is HOST.  The graph and the labels are validated
+ * on the device, and the verdict read, before any kernel indexes by them.
+ * Errors: LEIDEN_EINVAL (malformed graph, label out of range, bad gamma),
+ * LEIDEN_ENOMEM, LEIDEN_EOVERFLOW (nnz > 2^32 or 2m >= 2^40), LEIDEN_ECUDA. */
 int leiden_modularity(leiden_ctx *ctx, const leiden_csr *g, const int32_t *membership,
                       double gamma, double *q_out);
 
@@ -202,8 +204,11 @@ int leiden_ctx_set_timing(leiden_ctx *ctx, int32_t enable);
  * resolution gamma for membership (DEVICE [n], labels in [0, n)) on g, with
  * the same integer arithmetic as leiden_modularity; the work is ordered on
  * cuda_stream (cudaStream_t as void*, NULL = legacy default stream), which the
- * call synchronises before writing q_out (HOST).  Errors: LEIDEN_EINVAL (bad
- * gamma, malformed graph, label out of range), LEIDEN_ENOMEM (n too large),
+ * call synchronises before writing q_out (HOST).  The graph and the labels
+ * are validated, and the verdict read on the host, before any kernel indexes
+ * by them; the kernels that compute the terms test every index as well.
+ * Errors: LEIDEN_EINVAL (bad gamma, malformed graph, label out of range),
+ * LEIDEN_ENOMEM (n too large), LEIDEN_EOVERFLOW (nnz > 2^32 or 2m >= 2^40),
  * LEIDEN_ECUDA. */
 #define LEIDEN_NOALLOC_MAX_N 1048576
 int leiden_modularity_noalloc(const leiden_csr *g, const int32_t *membership, double gamma,

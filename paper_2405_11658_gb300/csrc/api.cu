@@ -621,15 +621,29 @@ int finish_two_m(leiden_ctx *c, Run &r, const leiden_csr *g) {
   return LEIDEN_OK;
 }
 
+// The u64 accumulators of Eq. 1 cannot wrap while nnz <= 2^32 (each weight is
+// below 2^31), and the 128-bit numerator q 2m inside - p sum Sigma^2 stays exact
+// while 2m < 2^40 (the bound every run checks).
+constexpr int64_t kModMaxNnz = (int64_t)1 << 32;
+
 int modularity_of(leiden_ctx *c, const leiden_csr *g, const int32_t *C, int64_t p, int64_t q, double *q_out) {
+  if (g->nnz > kModMaxNnz) return LEIDEN_EOVERFLOW;
   GraphView<int32_t> gv{g->n, g->off, g->idx, g->w};
-  launch_modularity_terms(gv, C, c->Ktmp, &c->ctr[CTR_SCRATCH0], c->st);
+  launch_modularity_terms(gv, g->nnz, C, c->Ktmp, &c->ctr[CTR_SCRATCH0], &c->ctr[CTR_ERROR], c->st);
   cudaMemcpyAsync(&c->h_ctr[CTR_SCRATCH0], &c->ctr[CTR_SCRATCH0], 4 * sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(&c->h_ctr[CTR_ERROR], &c->ctr[CTR_ERROR], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
   int rc = sync(c);
   if (rc) return rc;
+  if (c->h_ctr[CTR_ERROR]) {
+    // the callers validated the graph and the labels first, so this is an
+    // internal inconsistency; the kernels skipped every bad index
+    cudaMemsetAsync(&c->ctr[CTR_ERROR], 0, sizeof(u64), c->st);
+    return check_dev_flags(c, c->h_ctr[CTR_ERROR]);
+  }
   const int64_t inside = (int64_t)c->h_ctr[CTR_SCRATCH0];
   const i128 sq = read_i128(&c->h_ctr[CTR_SCRATCH0 + 1]);
   const int64_t two_m = (int64_t)c->h_ctr[CTR_SCRATCH0 + 3];
+  if (two_m < 0 || two_m >= ((int64_t)1 << 40)) return LEIDEN_EOVERFLOW;
   const i128 num = (i128)q * two_m * inside - (i128)p * sq;
   *q_out = two_m == 0 ? 0.0 : (double)num / ((double)two_m * (double)two_m * (double)q);
   return LEIDEN_OK;

@@ -199,9 +199,13 @@ void launch_renumber(int64_t n, int32_t *C, uint8_t *exists, int64_t *scanned, i
 void launch_lookup(int64_t n, int32_t *Ctop, const int32_t *Cp, cudaStream_t s);
 void launch_canonical(int64_t n, const int32_t *C, int32_t *out, int32_t *minv, uint8_t *flag,
                       int64_t *scanned, int64_t *tmp, cudaStream_t s);
+// Eq. 1 terms of membership C on g (nnz entries): acc[0] internal weight,
+// acc[1..2] sum of Sigma_c^2 (i128), acc[3] 2m.  Bounds-checked: a bad row,
+// label or column ID is skipped and sets 512 in *err; nothing runs when *err
+// is already set.
 template <typename WT>
-void launch_modularity_terms(GraphView<WT> g, const int32_t *C, int64_t *Sig_tmp, u64 *acc,
-                             cudaStream_t s);
+void launch_modularity_terms(GraphView<WT> g, int64_t nnz, const int32_t *C, int64_t *Sig_tmp, u64 *acc,
+                             u64 *err, cudaStream_t s);
 void launch_update_weights(int64_t count, const int32_t *src, const int32_t *dst,
                            const int32_t *w, int sign, const int32_t *Cprev, int64_t *K,
                            int64_t *Sig, cudaStream_t s);

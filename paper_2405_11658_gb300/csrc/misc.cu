@@ -165,25 +165,45 @@ void launch_canonical(int64_t n, const int32_t *C, int32_t *out, int32_t *minv, 
 // ---------------------------------------------------------------------------
 // Eq. 1 terms: acc[0] = sum of internal weight (sum_c sigma_c), acc[1..2] =
 // sum_c Sigma_c^2 (i128), acc[3] = 2m.
+//
+// Every index is tested before it is used -- the row bounds against [0, nnz],
+// the labels and column IDs against [0, n) -- so a malformed input can never
+// make these kernels read or write outside the arrays, whatever the caller
+// has or has not validated: an offending row or entry is skipped and sets
+// 512 in *err.  A kernel that finds *err already set (an earlier check on
+// the same stream failed) does nothing.
 // ---------------------------------------------------------------------------
 template <typename WT>
-__global__ void mod_rows_k(GraphView<WT> g, const int32_t *C, int64_t *Sig, u64 *acc) {
+__global__ void mod_rows_k(GraphView<WT> g, int64_t nnz, const int32_t *C, int64_t *Sig, u64 *acc,
+                           u64 *err) {
   __shared__ int64_t sbuf[32];
+  __shared__ int s_skip;
+  // one reading for the whole block, so no thread skips the barriers below
+  // while another waits at them
+  if (threadIdx.x == 0) s_skip = *(volatile u64 *)err != 0;
+  __syncthreads();
+  if (s_skip) return;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int64_t inside = 0, total = 0;
+  bool bad = false;
   for (int64_t i = w0; i < g.n; i += nw) {
+    const int64_t e0 = g.off[i], e1 = g.off[i + 1];
     const int32_t ci = C[i];
+    if (e0 < 0 || e1 < e0 || e1 > nnz || ci < 0 || (int64_t)ci >= g.n) { bad = true; continue; }
     int64_t k = 0;
-    for (int64_t e = g.off[i] + lane; e < g.off[i + 1]; e += 32) {
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
       const int64_t w = (int64_t)g.w[e];
+      const int32_t j = g.idx[e];
+      if (j < 0 || (int64_t)j >= g.n) { bad = true; continue; }
       k += w;
-      if (C[g.idx[e]] == ci) inside += w;
+      if (C[j] == ci) inside += w;
     }
     for (int o = 16; o; o >>= 1) k += shfl_xor_i64(k, o);
     if (lane == 0 && k) { atomic_add_i64(&Sig[ci], k); total += k; }
   }
+  if (bad) atomicOr(err, 512ull);
   inside = block_sum_i64(inside, sbuf);
   total = block_sum_i64(total, sbuf);
   if (threadIdx.x == 0) {
@@ -199,16 +219,18 @@ __global__ void mod_sq_k(int64_t n, const int64_t *Sig, u64 *acc) {
   if (threadIdx.x == 0 && s != 0) atomic_add_i128(&acc[1], s);
 }
 template <typename WT>
-void launch_modularity_terms(GraphView<WT> g, const int32_t *C, int64_t *Sig_tmp, u64 *acc,
-                             cudaStream_t s) {
+void launch_modularity_terms(GraphView<WT> g, int64_t nnz, const int32_t *C, int64_t *Sig_tmp, u64 *acc,
+                             u64 *err, cudaStream_t s) {
   cudaMemsetAsync(acc, 0, 4 * sizeof(u64), s);
   if (g.n <= 0) return;
   cudaMemsetAsync(Sig_tmp, 0, (size_t)g.n * sizeof(int64_t), s);
-  LK_COUNTED mod_rows_k<WT><<<grid_for(g.n * 32, 256, 152 * 32), 256, 0, s>>>(g, C, Sig_tmp, acc);
+  LK_COUNTED mod_rows_k<WT><<<grid_for(g.n * 32, 256, 152 * 32), 256, 0, s>>>(g, nnz, C, Sig_tmp, acc, err);
   LK_COUNTED mod_sq_k<<<grid_for(g.n, 256, 152 * 8), 256, 0, s>>>(g.n, Sig_tmp, acc);
 }
-template void launch_modularity_terms<int32_t>(GraphView<int32_t>, const int32_t *, int64_t *, u64 *, cudaStream_t);
-template void launch_modularity_terms<int64_t>(GraphView<int64_t>, const int32_t *, int64_t *, u64 *, cudaStream_t);
+template void launch_modularity_terms<int32_t>(GraphView<int32_t>, int64_t, const int32_t *, int64_t *, u64 *,
+                                               u64 *, cudaStream_t);
+template void launch_modularity_terms<int64_t>(GraphView<int64_t>, int64_t, const int32_t *, int64_t *, u64 *,
+                                               u64 *, cudaStream_t);
 
 // Sigma[c] = sum of K over members of c (Sigma zeroed first).
 __global__ void sigma_from_k(int64_t n, const int32_t *C, const int64_t *K, int64_t *Sig) {

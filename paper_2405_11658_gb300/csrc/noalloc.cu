@@ -52,6 +52,8 @@ extern "C" int leiden_modularity_noalloc(const leiden_csr *g, const int32_t *mem
                                          void *cuda_stream, double *q_out) {
   if (!g || !q_out || g->n < 0 || g->nnz < 0) return LEIDEN_EINVAL;
   if (g->n > LEIDEN_NOALLOC_MAX_N) return LEIDEN_ENOMEM;  // beyond the fixed scratch
+  // the u64 accumulators cannot wrap while nnz <= 2^32 (every weight < 2^31)
+  if (g->nnz > ((int64_t)1 << 32)) return LEIDEN_EOVERFLOW;
   if (!g->off || (g->n > 0 && !membership) || (g->nnz > 0 && (!g->idx || !g->w))) return LEIDEN_EINVAL;
   // gamma = p / q exactly, q = 2^20 before reduction
   const double scaled = gamma * 1048576.0;
@@ -71,19 +73,27 @@ extern "C" int leiden_modularity_noalloc(const leiden_csr *g, const int32_t *mem
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int64_t *sig = reinterpret_cast<int64_t *>(scr);
   unsigned long long *acc = scr + LEIDEN_NOALLOC_MAX_N;  // [0..3] terms, [8] error flag
-  // the array keeps the previous call's contents: clear what must start at 0
+  unsigned long long h[9] = {0};
+  // The array keeps the previous call's contents: clear what must start at 0.
+  // Validate the graph and the labels, and read the verdict on the host,
+  // before any kernel indexes by them.
   cudaMemsetAsync(acc + 8, 0, sizeof(unsigned long long), s);
   lk::launch_check_graph(g->n, g->nnz, g->off, g->idx, g->w, acc + 8, s);
   lk::launch_check_range(membership, g->n, g->n, acc + 8, s);
+  cudaMemcpyAsync(&h[8], acc + 8, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return LEIDEN_ECUDA;
+  if (h[8]) return LEIDEN_EINVAL;
+  // The terms kernels test every index themselves as well (a bad one is
+  // skipped and flagged), so no access depends on the order above.
   lk::GraphView<int32_t> gv{g->n, g->off, g->idx, g->w};
-  lk::launch_modularity_terms(gv, membership, sig, acc, s);  // zeroes sig[0..n) and acc[0..3]
-  unsigned long long h[9] = {0};
+  lk::launch_modularity_terms(gv, g->nnz, membership, sig, acc, acc + 8, s);  // zeroes sig[0..n), acc[0..3]
   cudaMemcpyAsync(h, acc, 9 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return LEIDEN_ECUDA;
   if (h[8]) return LEIDEN_EINVAL;
   const int64_t inside = (int64_t)h[0];
   const i128 sq = (i128)(((unsigned __int128)h[2] << 64) | (unsigned __int128)h[1]);
   const int64_t two_m = (int64_t)h[3];
+  if (two_m < 0 || two_m >= ((int64_t)1 << 40)) return LEIDEN_EOVERFLOW;
   const i128 num = (i128)q * two_m * inside - (i128)p * sq;
   *q_out = two_m == 0 ? 0.0 : (double)num / ((double)two_m * (double)two_m * (double)q);
   return LEIDEN_OK;

@@ -35,11 +35,14 @@ constexpr int SB_MAX_WARPS = 32;
 constexpr int SB_MAX_CLASSES = 256;
 
 // ---------------------------------------------------------------------------
-// Correctly rounded int128 -> double (round to nearest even): keep the top 64
-// significant bits with every lower bit folded into a sticky bit, convert that
-// (itself correctly rounded) and scale by the dropped power of two.  The
-// sticky bit sits below the rounding position of the 53-bit result, so the
-// two steps round exactly once.
+// Correctly rounded int128 -> double (round to nearest even) by round-to-odd
+// double rounding (Boldo and Melquiond, "When double rounding is odd", 2005):
+// truncate to the top 64 significant bits and OR every dropped bit into the
+// lowest kept bit (the sticky bit), which rounds the value to odd at 64 bits;
+// then convert those 64 bits to double (round to nearest even) and scale by
+// the dropped power of two.  A round-to-odd intermediate with at least two
+// more bits than the 53-bit target makes the second rounding equal to a
+// single correct rounding of the original value.
 // ---------------------------------------------------------------------------
 __device__ double i128_to_double(i128 x) {
   const bool neg = x < 0;
