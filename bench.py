@@ -1,12 +1,17 @@
-"""Benchmark: Static and Dynamic Frontier Leiden on an R-MAT scale-22 graph.
+"""Benchmark: Static and Dynamic Frontier Leiden on the largest single-GPU
+workload, a Chung-Lu web-graph stand-in with 2.0e9 CSR entries.
 
-Workload (one GPU): R-MAT scale 22, edge factor 16, (a, b, c, d) = (0.57,
-0.19, 0.19, 0.05), symmetrised, deduplicated, self-loops dropped, unit int32
-weights (4.19M vertices, ~1.3e8 CSR entries, ~1.1 GB of CSR: larger than the
-129 MB L2, so no flush is needed between steps).  Random batches of 1e-5,
-1e-4 and 1e-3 |E| undirected updates (80% insertions between uniform vertex
-pairs, 20% deletions of uniform existing edges, unit weight), each applied to
-the base graph separately (Sec. 5.1.4).
+Workload (one GPU, default): Chung-Lu with degree exponent 2.1 (endpoint
+probabilities proportional to (i + 10)^(-1/1.1), expected degrees capped at
+sqrt(2m)), 5e7 vertices, 1.0e9 undirected edges (2.0e9 CSR entries, int64
+offsets), integer weights uniform in 1..4, generated on the device; random
+batches of 1e-7 .. 1e-1 |E| undirected updates (decades; 80% insertions
+between uniform vertex pairs, 20% deletions of uniform existing edges, unit
+weight), each applied to the base graph separately (Sec. 5.1.4).  The CSR
+(16 GB) is far larger than the 129 MB L2, so no flush is needed between
+steps.  ``--workload rmat`` runs the R-MAT scale-22 workload instead (4.19M
+vertices, 1.3e8 entries, batches of 1e-5 .. 1e-3 |E|); its figures also
+appear in the default line under "rmat_s22".
 
 One step, all on the device: apply the step's batch to the base graph (a1),
 DF update from the base graph's membership (a2..a10), then Static Leiden on
@@ -37,21 +42,31 @@ sys.path.insert(0, ROOT)
 
 METRIC = "edges/s per Leiden pass; DF batch update time & p50/p99 vs GPU Static, same GPU"
 SCALE, EDGE_FACTOR = 22, 16
-BATCH_FRACS = (1e-5, 1e-4, 1e-3)
-GRAPH_SEED = 0x1EDE0 + 1
+RMAT_FRACS = (1e-5, 1e-4, 1e-3)
+RMAT_SEED = 0x1EDE0 + 1
+CL_N, CL_M = 50_000_000, 1_000_000_000
+CL_FRACS = (1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1)
+CL_SEED = 0x1EDE0 + 2
+# the oracle's bounded sample of the Chung-Lu workload: the same recipe at
+# 1/CL_SAMPLE_DIV of the vertices and edges
+CL_SAMPLE_DIV = 32
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=9)
+    ap.add_argument("--steps", type=int, default=14)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--sched", default="det", choices=["det", "async"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "serving", "lowdeg"])
+    ap.add_argument("--workload", default="cl", choices=["cl", "rmat", "serving", "lowdeg"])
+    ap.add_argument("--no-rmat-extra", action="store_true",
+                    help="skip the compact R-MAT scale-22 figures of the default Chung-Lu line")
+    ap.add_argument("--cl-div", type=int, default=1,
+                    help="--profile-static on the Chung-Lu recipe at 1/k of its vertices and edges")
     ap.add_argument("--profile-static", action="store_true",
                     help="run one Static Leiden on the workload graph and print its statistics (for profilers)")
     ap.add_argument("--lowdeg-samples", type=int, default=3, help="batches per size on the low-degree graphs")
@@ -90,7 +105,8 @@ def peaks():
 DECIDE_SOURCES = ("paper_2405_11658_gb300/csrc/move.cu", "paper_2405_11658_gb300/csrc/hub.cu",
                   "paper_2405_11658_gb300/csrc/internal.h", "paper_2405_11658_gb300/csrc/common.cuh",
                   "paper_2405_11658_gb300/csrc/api.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "decide_traffic_rmat22.json")
+TRAFFIC_FILES = {"cl": os.path.join(ROOT, "profiles", "decide_traffic_cl.json"),
+                 "rmat": os.path.join(ROOT, "profiles", "decide_traffic_rmat22.json")}
 
 
 def decide_sources_sha():
@@ -102,17 +118,22 @@ def decide_sources_sha():
     return h.hexdigest()
 
 
-def measured_traffic(scale):
+def measured_traffic(workload, entries_per_launch):
     """DRAM bytes per first-pass local-moving launch (one colour class) of the
-    decide kernels, from the ncu capture recorded in profiles/ -- or None when
-    there is none for this workload or the kernels changed since it was taken."""
+    decide kernels, from the ncu capture recorded in profiles/, scaled to this
+    run's entries per launch when the capture was taken on a smaller case --
+    or None when there is none for this workload or the kernels changed since
+    it was taken."""
     try:
-        with open(TRAFFIC_FILE) as f:
+        with open(TRAFFIC_FILES[workload]) as f:
             d = json.load(f)
-    except (OSError, ValueError):
+    except (OSError, ValueError, KeyError):
         return None
-    if d.get("scale") != scale or d.get("source_sha256") != decide_sources_sha():
+    if d.get("source_sha256") != decide_sources_sha():
         return None
+    per_entry = d.get("dram_bytes_per_scanned_entry")
+    if per_entry is not None and entries_per_launch:
+        return float(per_entry) * entries_per_launch
     return float(d["dram_bytes_per_launch"])
 
 
@@ -167,22 +188,104 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(scale, seed, nsteps):
-    from paper_2405_11658_gb300 import synth as S
-    g = S.rmat(scale, EDGE_FACTOR, 0.57, 0.19, 0.19, seed=seed)
-    nedges = len(g[1]) // 2
-    pairs = S.undirected_pairs(*g) if nsteps else None
-    batches = []
-    for k in range(nsteps):
-        frac = BATCH_FRACS[k % len(BATCH_FRACS)]
-        size = max(2, int(round(frac * nedges)))
-        batches.append((frac, S.random_batch(*g, size, seed=1000 + k, pairs=pairs)))
-    return g, batches
+def host_info():
+    """The host's core count and CPU model (the oracle's baseline runs on it)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:  # noqa: BLE001
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
-def cpu_baseline(g, max_passes=1):
+# ---------------------------------------------------------------------------
+# Workloads.  Each provides the device graph, one batch per step, the host
+# copy for the end-to-end leg and the oracle's bounded sample.
+# ---------------------------------------------------------------------------
+class RmatWorkload:
+    key = "rmat"
+
+    def __init__(self, scale=SCALE):
+        self.scale = scale
+        self.fracs = RMAT_FRACS
+
+    def config(self, n, nnz, sched, world):
+        return {"workload": f"rmat-s{self.scale}-ef{EDGE_FACTOR}: batch apply + DF update + Static Leiden",
+                "graph": f"R-MAT scale {self.scale}, edge factor {EDGE_FACTOR}, a/b/c/d=0.57/0.19/0.19/0.05",
+                "vertices": n, "csr_entries": nnz, "batch_fracs": list(self.fracs),
+                "schedule": sched, "l2": l2_note(8 * (n + 1) + 8 * nnz), "parallelism": f"replicas x{world}"}
+
+    def host_graph(self, seed):
+        from paper_2405_11658_gb300 import synth as S
+        return S.rmat(self.scale, EDGE_FACTOR, 0.57, 0.19, 0.19, seed=seed)
+
+    def build(self, L, dev, seed, nsteps):
+        """(G0, host (off, idx, w), [(frac, dE, iE)] per step, max_nnz)."""
+        from paper_2405_11658_gb300 import synth as S
+        g = self.host_graph(seed)
+        off, idx, w = g
+        pairs = S.undirected_pairs(*g)
+        nedges = len(pairs[0])
+        batches = []
+        for k in range(nsteps):
+            frac = self.fracs[k % len(self.fracs)]
+            d, i = S.random_batch(*g, max(2, int(round(frac * nedges))), seed=1000 + k, pairs=pairs)
+            batches.append((frac, L.Edges.from_numpy(d, device=dev), L.Edges.from_numpy(i, device=dev)))
+        max_nnz = len(idx) + 2 * max(b[2].count for b in batches) + 16
+        return L.Graph.from_numpy(off, idx, w, device=dev), g, batches, max_nnz
+
+    def cpu_sample(self):
+        g = self.host_graph(RMAT_SEED)
+        return g, (f"first pass of Static Leiden (DET) on the same R-MAT graph, {len(g[1])} CSR entries")
+
+
+class ChungLuWorkload:
+    key = "cl"
+
+    def __init__(self, n=CL_N, m=CL_M):
+        self.n, self.m = n, m
+        self.fracs = CL_FRACS
+
+    def config(self, n, nnz, sched, world):
+        return {"workload": f"chung-lu-{self.n:.0e}v-{2 * self.m:.1e}e: batch apply + DF update + Static Leiden",
+                "graph": "Chung-Lu, degree exponent 2.1, expected degrees capped at sqrt(2m), "
+                         "integer weights uniform in 1..4, generated on the device",
+                "vertices": n, "csr_entries": nnz, "batch_fracs": list(self.fracs),
+                "schedule": sched, "l2": l2_note(8 * (n + 1) + 8 * nnz), "parallelism": f"replicas x{world}"}
+
+    def build(self, L, dev, seed, nsteps):
+        import torch
+        from paper_2405_11658_gb300 import synth_device as D
+        (off, idx, w), (keys, wk) = D.chung_lu(self.n, self.m, 2.1, 1, 4, seed=seed, device=dev)
+        batches = []
+        for k in range(nsteps):
+            frac = self.fracs[k % len(self.fracs)]
+            d, i = D.random_batch(self.n, keys, wk, max(2, int(round(frac * self.m))), seed=1000 + k)
+            batches.append((frac, L.Edges(*d), L.Edges(*i)))
+        del keys, wk
+        torch.cuda.empty_cache()
+        max_nnz = idx.numel() + 2 * max(b[2].count for b in batches) + 16
+        return L.Graph(off, idx, w), None, batches, max_nnz
+
+    def cpu_sample(self):
+        from paper_2405_11658_gb300 import synth as S
+        n, m = self.n // CL_SAMPLE_DIV, self.m // CL_SAMPLE_DIV
+        g = S.chung_lu(n, m, 2.1, 1, 4, seed=CL_SEED)
+        return g, (f"first pass of Static Leiden (DET) on a Chung-Lu graph of the same recipe at "
+                   f"1/{CL_SAMPLE_DIV} of the vertices and edges ({n} vertices, {len(g[1])} CSR entries)")
+
+
+WORKLOADS = {"cl": ChungLuWorkload, "rmat": RmatWorkload}
+
+
+def cpu_baseline(g, sample, max_passes=1):
     """The oracle as it stands, single-threaded, on the first pass of Static
-    Leiden over the same graph: CSR entries per second of that pass."""
+    Leiden over a bounded sample of the workload: CSR entries per second of
+    that pass."""
     import oracle as O
     t0 = time.perf_counter()
     r = O.static(*g, O.LeidenOpts(max_passes=max_passes))
@@ -191,9 +294,7 @@ def cpu_baseline(g, max_passes=1):
     edges = sum(st["nnz"][:st["passes"]])
     secs = sum(st["t_pass"][:st["passes"]])
     return {"value": edges / secs, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {max_passes} pass(es) of Static Leiden (DET) on the same R-MAT graph, "
-                      f"{st['nnz'][0]} CSR entries; {wall:.1f} s of CPU work",
-            "seconds": round(wall, 3)}
+            "sample": f"{sample}; {wall:.1f} s of CPU work", "seconds": round(wall, 3), "host": host_info()}
 
 
 def l2_note(csr_bytes):
@@ -203,35 +304,32 @@ def l2_note(csr_bytes):
     return f"inputs smaller than L2 (CSR {csr_bytes / 1e6:.0f} MB): L2-warm steps, no flush"
 
 
-def workload_config(scale, n, nnz, sched, world):
-    """The benchmark workload's config object (both arms print the same one)."""
-    return {"workload": f"rmat-s{scale}-ef{EDGE_FACTOR}: batch apply + DF update + Static Leiden",
-            "graph": f"R-MAT scale {scale}, edge factor {EDGE_FACTOR}, a/b/c/d=0.57/0.19/0.19/0.05",
-            "vertices": n, "csr_entries": nnz, "batch_fracs": list(BATCH_FRACS),
-            "schedule": sched, "l2": l2_note(8 * (n + 1) + 8 * nnz),
-            "parallelism": f"replicas x{world}"}
+def workload_of(args):
+    return RmatWorkload(args.scale) if args.workload == "rmat" else ChungLuWorkload()
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    g, _ = make_inputs(args.scale, GRAPH_SEED, 0)
+    wl = workload_of(args)
+    g, sample = wl.cpu_sample()
     vals = []
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(g))
+        vals.append(cpu_baseline(g, sample))
     total = time.perf_counter() - t0
     v = statistics.mean(x["value"] for x in vals)
+    n, nnz = (wl.n, 2 * wl.m) if wl.key == "cl" else (len(g[0]) - 1, len(g[1]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
-            "config": workload_config(args.scale, len(g[0]) - 1, len(g[1]), args.sched, world),
+            "config": wl.config(n, nnz, args.sched, world),
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[0]["sample"], "value": v,
-                             "unit": "edges/s"},
+                             "unit": "edges/s", "host": vals[0]["host"]},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -252,46 +350,35 @@ def combine_ranks(total_ms, static_ms, edges, launches, world, device):
     return float(t[0]), float(t[1]), float(e[0]), int(e[1])
 
 
-def run_ours(args):
+def run_graph(args, wl, L, dev, stream, rank, world, steps, warmup, e2e_steps, with_clocks=True):
+    """The timed steps of one graph workload on this rank; returns the
+    figures (device times are this rank's, not yet combined)."""
     import torch
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    import paper_2405_11658_gb300 as L
-    dev = torch.device("cuda", torch.cuda.current_device())
-    nsteps = args.warmup + args.steps
-    g, batches = make_inputs(args.scale, GRAPH_SEED + 7919 * rank, nsteps)
-    off, idx, w = g
-    n, nnz = len(off) - 1, len(idx)
-    max_nnz = nnz + 2 * max(len(b[1][0]) for _, b in batches) + 16
-    stream = torch.cuda.current_stream()
+    nsteps = warmup + steps
+    seed = (CL_SEED if wl.key == "cl" else RMAT_SEED) + 7919 * rank
+    G0, host, batches, max_nnz = wl.build(L, dev, seed, nsteps)
+    n, nnz = G0.n, G0.nnz
     opts = L.Opts(sched=L.DET if args.sched == "det" else L.ASYNC)
-    G0 = L.Graph.from_numpy(off, idx, w, device=dev)
-    dev_batches = [(f, L.Edges.from_numpy(d, device=dev), L.Edges.from_numpy(i, device=dev))
-                   for f, (d, i) in batches]
     ctx = L.Context(max_n=n, max_nnz=max_nnz, stream=stream)
     Cs, _ = ctx.static(G0, opts, want_q=False)
     # base membership with consistent auxiliary information (K, Sigma): one
     # ND pass over the unchanged graph returns C0 together with K0 and S0
     C0, K0, S0, _ = ctx.update(G0, Cs, None, None, "ND", opts, want_q=False)
-
+    del Cs
     rec = []
 
     def step(k, timed):
-        frac, dE, iE = dev_batches[k]
+        frac, dE, iE = batches[k]
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
         Gt = ctx.apply_batch(G0, dE, iE, cap_nnz=max_nnz)
         ev[1].record(stream)
-        memb, _, _, qdf = ctx.update(Gt, C0, dE, iE, "DF", opts, prior_K=K0, prior_Sigma=S0, want_q=False)
+        ctx.update(Gt, C0, dE, iE, "DF", opts, prior_K=K0, prior_Sigma=S0, want_q=False)
         ev[2].record(stream)
+        st_df = ctx.stats()
         if timed:
             ctx.set_timing(True)
-        ms, _ = ctx.static(Gt, opts, want_q=False)
+        ctx.static(Gt, opts, want_q=False)
         ev[3].record(stream)
         if timed:
             ctx.set_timing(False)
@@ -299,70 +386,50 @@ def run_ours(args):
         torch.cuda.synchronize()
         t = [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
         rec.append({"frac": frac, "apply_ms": t[0], "df_ms": t[1], "static_ms": t[2],
-                    "static_edges": sum(st["nnz"][:st["passes"]]), "stats": st})
+                    "static_edges": sum(st["nnz"][:st["passes"]]), "stats": st,
+                    "df_affected0": st_df["affected0"]})
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         step(k, False)
     rec.clear()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    with Clocks(torch.cuda.current_device()) as clk:
-        launches0 = L.kernel_launches()
-        t0 = time.perf_counter()
-        e_start = torch.cuda.Event(enable_timing=True)
-        e_end = torch.cuda.Event(enable_timing=True)
-        e_start.record(stream)
-        for k in range(args.warmup, nsteps):
-            step(k, True)
-        e_end.record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        launches = L.kernel_launches() - launches0
-    total_ms = e_start.elapsed_time(e_end)
-    static_ms = sum(r["static_ms"] for r in rec)
-    static_edges = sum(r["static_edges"] for r in rec)
-    # max over ranks of the device time
-    total_ms, static_ms, static_edges_all, launches = combine_ranks(total_ms, static_ms, static_edges, launches,
-                                                                     world, dev)
-    value = static_edges_all / (static_ms / 1000.0)
+    clk = Clocks(torch.cuda.current_device()) if with_clocks else None
+    if clk:
+        clk.__enter__()
+    launches0 = L.kernel_launches()
+    t0 = time.perf_counter()
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for k in range(warmup, nsteps):
+        step(k, True)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = L.kernel_launches() - launches0
+    if clk:
+        clk.__exit__(None, None, None)
+    out = {"n": n, "nnz": nnz, "rec": rec, "total_ms": e_start.elapsed_time(e_end), "wall": wall,
+           "launches": launches, "clocks": clk.summary() if clk else None}
 
-    # roofline of the dominant kernel family: the local-moving decide kernels
-    # of the first pass (every vertex of the input graph, the same work in
-    # every step), one launch = the decide kernels of one colour class
-    mv_bytes = sum(r["stats"]["move0_bytes"] for r in rec)
-    mv_ms = sum(r["stats"]["move0_kernel_ms"] for r in rec)
-    mv_launches = sum(r["stats"]["move0_kernel_launches"] for r in rec)
-    all_bytes = sum(r["stats"]["move_bytes"] for r in rec)
-    all_ms = sum(r["stats"]["move_kernel_ms"] for r in rec)
-    peak, peak_kind = peaks()
-    achieved = (mv_bytes / mv_launches) / ((mv_ms / mv_launches) / 1000.0) / 1e9 if mv_ms > 0 else None
-
-    # DF vs Static per batch size
-    df = {}
-    for frac in BATCH_FRACS:
-        rs = [r for r in rec if r["frac"] == frac]
-        if not rs:
-            continue
-        d = sorted(r["df_ms"] for r in rs)
-        s = sorted(r["static_ms"] for r in rs)
-        df[f"{frac:g}"] = {"df_ms_p50": float(np.percentile(d, 50)), "df_ms_p99": float(np.percentile(d, 99)),
-                           "static_ms_p50": float(np.percentile(s, 50)),
-                           "speedup_vs_static": float(np.median(s) / np.median(d)),
-                           "apply_ms_p50": float(np.median([r["apply_ms"] for r in rs])), "samples": len(rs)}
-
-    # end to end through the public API from pinned host buffers
-    e2e = None
-    if args.e2e_steps > 0:
-        off_h = torch.from_numpy(off).pin_memory()
-        idx_h = torch.from_numpy(idx).pin_memory()
-        w_h = torch.from_numpy(w).pin_memory()
+    # end to end through the public API from pinned host buffers: the graph
+    # copied in, Static Leiden, the labels copied out, every step
+    if e2e_steps > 0:
+        if host is None:
+            host = (G0.off.cpu().numpy(), G0.idx.cpu().numpy(), G0.w.cpu().numpy())
+        off_h = torch.from_numpy(host[0]).pin_memory()
+        idx_h = torch.from_numpy(host[1]).pin_memory()
+        w_h = torch.from_numpy(host[2]).pin_memory()
         m_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        del G0, batches
+        torch.cuda.empty_cache()
         Gd = L.Graph(torch.empty_like(off_h, device=dev), torch.empty_like(idx_h, device=dev),
                      torch.empty_like(w_h, device=dev))
         mdev = torch.empty(n, dtype=torch.int32, device=dev)
         e_edges, e_ms = 0, 0.0
-        for k in range(args.e2e_steps + 1):
+        for k in range(e2e_steps + 1):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -378,37 +445,113 @@ def run_ours(args):
             if k > 0:  # the first round is a warm-up
                 e_edges += sum(st["nnz"][:st["passes"]])
                 e_ms += a.elapsed_time(b)
-        e2e = {"value": e_edges / (e_ms / 1000.0), "unit": "edges/s",
-               "h2d_bytes_per_step": int(off.nbytes + idx.nbytes + w.nbytes), "d2h_bytes_per_step": int(n * 4)}
+        out["e2e"] = {"value": e_edges / (e_ms / 1000.0), "unit": "edges/s",
+                      "h2d_bytes_per_step": int(off_h.nbytes + idx_h.nbytes + w_h.nbytes),
+                      "d2h_bytes_per_step": int(n * 4)}
+        del Gd, off_h, idx_h, w_h
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def summarise(wl, out, static_ms, static_edges):
+    """Per-batch-size DF / Static figures and the first-pass decide roofline."""
+    rec = out["rec"]
+    df = {}
+    for frac in wl.fracs:
+        rs = [r for r in rec if r["frac"] == frac]
+        if not rs:
+            continue
+        d = sorted(r["df_ms"] for r in rs)
+        s = sorted(r["static_ms"] for r in rs)
+        df[f"{frac:g}"] = {"df_ms_p50": float(np.percentile(d, 50)), "df_ms_p99": float(np.percentile(d, 99)),
+                           "static_ms_p50": float(np.percentile(s, 50)),
+                           "speedup_vs_static": float(np.median(s) / np.median(d)),
+                           "apply_ms_p50": float(np.median([r["apply_ms"] for r in rs])),
+                           "df_affected0_p50": int(np.median([r["df_affected0"] for r in rs])),
+                           "samples": len(rs)}
+    # roofline of the dominant kernel family: the local-moving decide kernels
+    # of the first pass (every vertex of the input graph, the same work in
+    # every step), one launch = the decide kernels of one colour class
+    mv_bytes = sum(r["stats"]["move0_bytes"] for r in rec)
+    mv_ms = sum(r["stats"]["move0_kernel_ms"] for r in rec)
+    mv_launches = sum(r["stats"]["move0_kernel_launches"] for r in rec)
+    mv_entries = sum(r["stats"]["move0_scanned_entries"] for r in rec)
+    all_bytes = sum(r["stats"]["move_bytes"] for r in rec)
+    all_ms = sum(r["stats"]["move_kernel_ms"] for r in rec)
+    peak, peak_kind = peaks()
+    achieved = (mv_bytes / mv_launches) / ((mv_ms / mv_launches) / 1000.0) / 1e9 if mv_ms > 0 else None
+    last = rec[-1]["stats"] if rec else {}
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": measured_traffic(wl.key, mv_entries / max(1, mv_launches)),
+            "kernel": "first-pass local-move decide kernels (all degree tiers), per colour class",
+            "peak_kind": peak_kind,
+            "bytes_per_launch": mv_bytes / max(1, mv_launches),
+            "ms_per_launch": mv_ms / max(1, mv_launches), "launches": mv_launches,
+            "entries_per_launch": mv_entries / max(1, mv_launches),
+            "all_passes_achieved": (all_bytes / (all_ms / 1000.0) / 1e9) if all_ms else None}
+    return {"static_ms_mean": static_ms / max(1, len(rec)), "static_edges_per_s": static_edges / (static_ms / 1000.0),
+            "static_passes": last.get("passes"), "static_iters": last.get("iters"),
+            "static_nnz_per_pass": last.get("nnz"), "df": df, "roofline": roof}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2405_11658_gb300 as L
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    wl = workload_of(args)
+    out = run_graph(args, wl, L, dev, stream, rank, world, args.steps, args.warmup, args.e2e_steps)
+    rec = out["rec"]
+    static_ms = sum(r["static_ms"] for r in rec)
+    static_edges = sum(r["static_edges"] for r in rec)
+    # max over ranks of the device time
+    total_ms, static_ms_all, static_edges_all, launches = combine_ranks(out["total_ms"], static_ms, static_edges,
+                                                                         out["launches"], world, dev)
+    value = static_edges_all / (static_ms_all / 1000.0)
+    summ = summarise(wl, out, static_ms, static_edges)
+
+    # the R-MAT scale-22 figures beside the Chung-Lu line (not timed into it)
+    rmat = None
+    if wl.key == "cl" and not args.no_rmat_extra:
+        rw = RmatWorkload(SCALE)
+        ro = run_graph(args, rw, L, dev, stream, rank, world, 6, 3, 0, with_clocks=False)
+        r_ms = sum(r["static_ms"] for r in ro["rec"])
+        r_edges = sum(r["static_edges"] for r in ro["rec"])
+        rs = summarise(rw, ro, r_ms, r_edges)
+        rmat = {"config": rw.config(ro["n"], ro["nnz"], args.sched, world), "value": r_edges / (r_ms / 1000.0),
+                "unit": "edges/s", **{k: rs[k] for k in ("static_ms_mean", "static_passes", "df")},
+                "roofline_frac": rs["roofline"]["frac"], "roofline_achieved": rs["roofline"]["achieved"]}
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
-        base = cpu_baseline(g)
+        g, sample = wl.cpu_sample()
+        base = cpu_baseline(g, sample)
 
-    ctx.close()
     if rank == 0:
-        last = rec[-1]["stats"] if rec else {}
         line = {
             "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": workload_config(args.scale, n, nnz, args.sched, world),
-            "static_ms_mean": static_ms / max(1, len(rec)),
-            "static_passes": last.get("passes"), "static_iters": last.get("iters"),
-            "df": df,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": measured_traffic(args.scale),
-                         "kernel": "first-pass local-move decide kernels (all degree tiers), per colour class",
-                         "peak_kind": peak_kind,
-                         "bytes_per_launch": mv_bytes / max(1, mv_launches),
-                         "ms_per_launch": mv_ms / max(1, mv_launches), "launches": mv_launches,
-                         "all_passes_achieved": (all_bytes / (all_ms / 1000.0) / 1e9) if all_ms else None},
+            "config": wl.config(out["n"], out["nnz"], args.sched, world),
+            **{k: summ[k] for k in ("static_ms_mean", "static_passes", "static_iters", "static_nnz_per_pass", "df")},
+            "roofline": summ["roofline"],
             "cpu_baseline": base,
-            "e2e": e2e,
+            "e2e": out.get("e2e"),
             "gpu_launches": launches,
-            "clocks": clk.summary(),
-            "wall_s": wall,
+            "clocks": out["clocks"],
+            "wall_s": out["wall"],
         }
+        if rmat is not None:
+            line["rmat_s22"] = rmat
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -686,17 +829,28 @@ def run_lowdeg(args):
 
 
 def run_profile_static(args):
-    """One Static Leiden (DET) on the benchmark graph with the decide kernels
-    timed; prints the run's statistics as one JSON line.  A profiler run over
-    this command sees exactly one run's launches (local-moving inside the
-    NVTX range "local_move", refinement in "refine", aggregation in
+    """One Static Leiden (DET) on the workload's graph (``--workload cl`` or
+    ``rmat``; ``--cl-div k`` takes the Chung-Lu recipe at 1/k of the vertices
+    and edges) with the decide kernels timed; prints the run's statistics as
+    one JSON line.  A profiler run over this command sees exactly one run's
+    launches (local-moving inside the NVTX range "local_move", its first pass
+    in "local_move_pass0", refinement in "refine", aggregation in
     "aggregate")."""
     import torch
     torch.cuda.set_device(0)
     import paper_2405_11658_gb300 as L
-    g, _ = make_inputs(args.scale, GRAPH_SEED, 0)
-    G = L.Graph.from_numpy(*g)
-    with L.Context(max_n=len(g[0]) - 1, max_nnz=len(g[1]) + 16) as ctx:
+    if args.workload == "cl":
+        from paper_2405_11658_gb300 import synth_device as D
+        n, m = CL_N // args.cl_div, CL_M // args.cl_div
+        (off, idx, w), _ = D.chung_lu(n, m, 2.1, 1, 4, seed=CL_SEED, device="cuda")
+        torch.cuda.empty_cache()
+        G = L.Graph(off, idx, w)
+        name = f"chung-lu {n} vertices {2 * m} entries static leiden"
+    else:
+        g = RmatWorkload(args.scale).host_graph(RMAT_SEED)
+        G = L.Graph.from_numpy(*g)
+        name = f"rmat-s{args.scale}-ef{EDGE_FACTOR} static leiden"
+    with L.Context(max_n=G.n, max_nnz=G.nnz + 16) as ctx:
         ctx.set_timing(True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -706,9 +860,9 @@ def run_profile_static(args):
         st = ctx.stats()
     keep = ("passes", "iters", "nv", "nnz", "moves", "refine_moves", "move_kernel_ms", "move_kernel_launches",
             "move_scanned_entries", "move_scanned_vertices", "move_bytes", "move0_kernel_ms",
-            "move0_kernel_launches", "move0_bytes", "t_move_ms", "t_refine_ms", "t_agg_ms")
-    print(json.dumps({"workload": f"rmat-s{args.scale}-ef{EDGE_FACTOR} static leiden", "ms": ms, "q": q,
-                      **{k: st[k] for k in keep}}))
+            "move0_kernel_launches", "move0_bytes", "move0_scanned_entries", "t_move_ms", "t_refine_ms",
+            "t_agg_ms", "wide_passes")
+    print(json.dumps({"workload": name, "ms": ms, "q": q, **{k: st[k] for k in keep}}))
     return 0
 
 

@@ -179,6 +179,10 @@ typedef struct {
   double move0_kernel_ms;
   int64_t move0_kernel_launches;
   double move0_bytes;
+  /* bit p set: pass p compared candidate scores in 128 bits, because a
+   * super-vertex's K' times 2m reached 2^62 (otherwise 64 bits suffice) */
+  uint32_t wide_passes;
+  int64_t move0_scanned_entries;                /* CSR entries the first pass's decide kernels read */
 } leiden_run_stats;
 
 /* Copies the statistics of the last run into *out (HOST). */

@@ -68,7 +68,8 @@ class _Stats(C.Structure):
                 ("move_bytes", C.c_double), ("total_ms", C.c_double),
                 ("t_move_ms", C.c_double * STATS_PASSES), ("t_refine_ms", C.c_double * STATS_PASSES),
                 ("t_agg_ms", C.c_double * STATS_PASSES), ("t_pass_ms", C.c_double * STATS_PASSES),
-                ("move0_kernel_ms", C.c_double), ("move0_kernel_launches", C.c_int64), ("move0_bytes", C.c_double)]
+                ("move0_kernel_ms", C.c_double), ("move0_kernel_launches", C.c_int64), ("move0_bytes", C.c_double),
+                ("wide_passes", C.c_uint32), ("move0_scanned_entries", C.c_int64)]
 
     def as_dict(self) -> dict:
         k = min(self.passes, STATS_PASSES)

@@ -191,7 +191,6 @@ struct Run {
   const leiden_opts *o;
   int64_t p, q, two_m, A;
   int log2S;
-  bool wide;  // 128-bit scores needed
   bool dynamic;
   const uint8_t *in_range0;  // DS affected range in pass 0
   int64_t N;                 // vertices of the input graph
@@ -236,19 +235,28 @@ struct Buckets {
   int64_t koff[MAX_KEYS + 1];
   int nkeys;
   int64_t maxdeg;
+  int64_t kmax;  // largest weighted degree K' of the level
 };
 
-__global__ void maxdeg_k(const int64_t *off, int64_t n, u64 *out) {
-  u64 m = 0;
+// out[0] = largest row length, out[1] = largest K'[i] of the level.
+__global__ void maxdeg_k(const int64_t *off, const int64_t *K, int64_t n, u64 *out) {
+  u64 m = 0, mk = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const u64 d = (u64)(off[i + 1] - off[i]);
     if (d > m) m = d;
+    const u64 k = (u64)K[i];
+    if (k > mk) mk = k;
   }
   for (int o = 16; o; o >>= 1) {
     const u64 y = __shfl_xor_sync(FULL_MASK, m, o);
     if (y > m) m = y;
+    const u64 z = __shfl_xor_sync(FULL_MASK, mk, o);
+    if (z > mk) mk = z;
   }
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+  if ((threadIdx.x & 31) == 0) {
+    if (m) atomicMax(&out[0], m);
+    if (mk) atomicMax(&out[1], mk);
+  }
 }
 
 __global__ void count_u8_k(const uint8_t *a, int64_t n, u64 *out) {
@@ -271,15 +279,30 @@ int build_buckets(const Run &r, const int64_t *off, int64_t n, Buckets &b) {
   leiden_ctx *c = r.c;
   b.nkeys = (1 << r.log2S) * c->tiers.ntiers;
   launch_buckets(off, n, r.log2S, c->tiers, c->vlist, c->blockhist, c->scanned, c->koff_dev, c->scan_tmp, c->st);
-  cudaMemsetAsync(&c->ctr[CTR_SCRATCH0], 0, sizeof(u64), c->st);
-  if (n > 0) LK_COUNTED maxdeg_k<<<c->sms * 4, 256, 0, c->st>>>(off, n, &c->ctr[CTR_SCRATCH0]);
+  cudaMemsetAsync(&c->ctr[CTR_SCRATCH0], 0, 2 * sizeof(u64), c->st);
+  if (n > 0) LK_COUNTED maxdeg_k<<<c->sms * 4, 256, 0, c->st>>>(off, c->Kp, n, &c->ctr[CTR_SCRATCH0]);
   cudaMemcpyAsync(c->h_koff, c->koff_dev, (size_t)(b.nkeys + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c->st);
-  cudaMemcpyAsync(&c->h_ctr[CTR_SCRATCH0], &c->ctr[CTR_SCRATCH0], sizeof(u64), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(&c->h_ctr[CTR_SCRATCH0], &c->ctr[CTR_SCRATCH0], 2 * sizeof(u64), cudaMemcpyDeviceToHost, c->st);
   int rc = sync(c);
   if (rc) return rc;
   memcpy(b.koff, c->h_koff, (size_t)(b.nkeys + 1) * sizeof(int64_t));
   b.maxdeg = (int64_t)c->h_ctr[CTR_SCRATCH0];
+  b.kmax = (int64_t)c->h_ctr[CTR_SCRATCH0 + 1];
   return LEIDEN_OK;
+}
+
+// Width of the decide kernels' candidate scores for one level.  A vertex i
+// compares its candidates by A K_{i->c} - p K_i Sigma'_c (Eq. 2 scaled by
+// 2m^2 q, without the terms common to all candidates); with K_{i->c} <= K_i
+// and Sigma'_c <= 2m both products lie in [0, K_i 2m max(p, q)], so while
+// Kmax 2m max(p, q) < 2^62 every score fits 64 bits, and while Kmax < 2^31
+// every summed K_{i->c} fits the 32-bit table values.  Only levels with a
+// super-vertex of a large share of 2m need 128 bits.  The move itself (the
+// full Eq. 2 score, its sum over the iteration) is always 128-bit, so the
+// width changes no decision.
+bool narrow_scores(const Run &r, const Buckets &b) {
+  const int64_t pq = r.p > r.q ? r.p : r.q;
+  return b.kmax < ((int64_t)1 << 31) && (i128)b.kmax * r.two_m * pq < ((i128)1 << 62);
 }
 
 // Launch the decide kernels of every tier of colour class s.  The tiers
@@ -398,6 +421,7 @@ int local_move(Run &r, GraphView<WT> g, const Buckets &b, bool first_pass, doubl
   c->stats.move_bytes += bytes;
   if (first_pass) {
     c->stats.move0_bytes += bytes;
+    c->stats.move0_scanned_entries += ent;
     c->stats.move0_kernel_launches = c->stats.move_kernel_launches;  // the first pass's launches come first
   }
   return li;
@@ -454,15 +478,28 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
 }
 
 template <typename WT, typename ST>
+int pass_body(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, int64_t *nnz_out,
+              const Buckets &b, std::chrono::steady_clock::time_point t_start);
+
+template <typename WT>
 int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, int64_t *nnz_out) {
+  const auto t_start = std::chrono::steady_clock::now();
+  Buckets b;
+  int rc = build_buckets(r, g.off, g.n, b);
+  if (rc) return rc;
+  if (b.koff[b.nkeys] != g.n) return LEIDEN_ECUDA;
+  if (!LK_FORCE_WIDE_SCORES && narrow_scores(r, b)) return pass_body<WT, int64_t>(r, g, lp, tau, dst, nc_out, nnz_out, b, t_start);
+  if (lp < LEIDEN_STATS_PASSES) r.c->stats.wide_passes |= 1u << lp;
+  return pass_body<WT, i128>(r, g, lp, tau, dst, nc_out, nnz_out, b, t_start);
+}
+
+template <typename WT, typename ST>
+int pass_body(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, int64_t *nnz_out,
+              const Buckets &b, std::chrono::steady_clock::time_point t_start) {
   leiden_ctx *c = r.c;
   const int64_t nv = g.n;
-  const auto t_start = std::chrono::steady_clock::now();
   const bool rec = lp < LEIDEN_STATS_PASSES;
-  Buckets b;
-  int rc = build_buckets(r, g.off, nv, b);
-  if (rc) return rc;
-  if (b.koff[b.nkeys] != nv) return LEIDEN_ECUDA;
+  int rc;
   if (b.maxdeg > 0) {
     int lh = 1;
     while (((int64_t)1 << lh) < 2 * b.maxdeg) lh++;
@@ -532,8 +569,9 @@ int pass(Run &r, GraphView<WT> g, int lp, double tau, int dst, int64_t *nc_out, 
   return 0;
 }
 
-template <typename ST>
-int run_leiden_st(Run &r, const leiden_csr *g0) {
+int run_leiden(Run &r, const leiden_csr *g0) {
+  // the first pass uses the input graph directly (int32 weights), later
+  // passes the workspace (int64); each pass picks its score width
   leiden_ctx *c = r.c;
   const int64_t N = g0->n;
   launch_iota(c->Ctop, N, c->st);
@@ -548,8 +586,8 @@ int run_leiden_st(Run &r, const leiden_csr *g0) {
     if (lp < LEIDEN_STATS_PASSES) c->stats.nnz[lp] = nnz_cur;
     const int dst = cur < 0 ? 0 : 1 - cur;
     int64_t nc = 0, nnz2 = 0;
-    int rc = cur < 0 ? pass<int32_t, ST>(r, g32, lp, tau, dst, &nc, &nnz2)
-                     : pass<int64_t, ST>(r, g64, lp, tau, dst, &nc, &nnz2);
+    int rc = cur < 0 ? pass<int32_t>(r, g32, lp, tau, dst, &nc, &nnz2)
+                     : pass<int64_t>(r, g64, lp, tau, dst, &nc, &nnz2);
     if (rc < 0) return rc;
     if (rc == 1) break;
     // next level: K' = Sigma' = row sums (written by the aggregation), C' =
@@ -566,13 +604,6 @@ int run_leiden_st(Run &r, const leiden_csr *g0) {
   }
   launch_lookup(N, c->Ctop, c->Cp, c->st);
   return check_cuda(c);
-}
-
-int run_leiden(Run &r, const leiden_csr *g0) {
-  // the level-0 nnz is recorded by the caller's stats; the first pass uses the
-  // input graph directly (int32 weights), later passes the workspace (int64)
-  if (r.wide) return run_leiden_st<i128>(r, g0);
-  return run_leiden_st<int64_t>(r, g0);
 }
 
 // Device-side validation of a caller's CSR (off, idx, w); LEIDEN_EINVAL on a
@@ -616,8 +647,6 @@ int finish_two_m(leiden_ctx *c, Run &r, const leiden_csr *g) {
   r.two_m = (int64_t)c->h_ctr[CTR_SCRATCH0];
   if (r.two_m < 0 || r.two_m >= ((int64_t)1 << 40)) return LEIDEN_EOVERFLOW;
   r.A = r.two_m * r.q;
-  const i128 bound = (i128)4 * r.two_m * r.two_m * (r.p > r.q ? r.p : r.q);
-  r.wide = bound >= ((i128)1 << 62);
   return LEIDEN_OK;
 }
 

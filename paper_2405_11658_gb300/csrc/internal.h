@@ -113,6 +113,11 @@ static constexpr int64_t HUB_TABLE_MIN = 4096;
 #ifndef LK_HUB_ROUND_SLOTS
 #define LK_HUB_ROUND_SLOTS 0
 #endif
+// 1: every level compares candidate scores in 128 bits, whatever its
+// largest K' (a testing aid: both widths must give the same decisions).
+#ifndef LK_FORCE_WIDE_SCORES
+#define LK_FORCE_WIDE_SCORES 0
+#endif
 #ifndef LK_AUX_STREAMS
 #define LK_AUX_STREAMS 6
 #endif

@@ -112,6 +112,28 @@ def test_static_det_options(ctx, S_, gamma, tol):
     assert_stats_equal(st, ref.stats)
 
 
+def heavy_graph(seed):
+    # four planted blocks with weights up to 2^20: 2m ~ 5e10, so the first
+    # level's scores fit 64 bits (largest K times 2m below 2^62) and the
+    # aggregated levels, whose super-vertices carry a quarter of 2m, need 128
+    off, idx, _ = S.planted_partition(4000, 4, 0.02, 0.001, seed)
+    u, v, _ = S.undirected_pairs(off, idx)
+    w = np.random.default_rng(seed).integers(1, 2**20, size=len(u))
+    return S.edges_to_csr(4000, u, v, w)
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.5])
+def test_score_width_per_level_is_bit_exact(ctx, gamma):
+    g = heavy_graph(17)
+    ref = O.static(*g, O.LeidenOpts(gamma=gamma))
+    memb, q, st = run_static(ctx, g, L.Opts(gamma=gamma))
+    assert np.array_equal(memb, ref.membership)
+    assert q == ref.q
+    assert_stats_equal(st, ref.stats)
+    # both widths ran: 64-bit scores in the first pass, 128-bit in a later one
+    assert not st["wide_passes"] & 1 and st["wide_passes"] >> 1, st["wide_passes"]
+
+
 def test_static_max_passes_and_iters(ctx):
     g = S.planted_partition(3000, 6, 0.02, 0.002, 5)
     for mp, mi in ((1, 20), (2, 3), (10, 1)):

@@ -65,3 +65,53 @@ def valid_csr(off, idx, w):
     lambda: S.ring_of_cliques(6, 4)])
 def test_generated_graphs_are_valid_symmetric_csr(make):
     valid_csr(*make())
+
+
+# ---------------------------------------------------------------------------
+# The device generators (torch), run here on the CPU device.
+# ---------------------------------------------------------------------------
+torch = pytest.importorskip("torch")
+from paper_2405_11658_gb300 import synth_device as D  # noqa: E402
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_device_csr_builder_matches_the_host_builder(seed):
+    (off, idx, w), (keys, wk) = D.chung_lu(3000, 12000, 2.1, 1, 4, seed=seed, device="cpu")
+    k = keys.numpy()
+    assert len(k) == 12000 and np.all(np.diff(k) > 0)      # exactly m distinct edges, sorted
+    assert np.all(k // 3000 < k % 3000)                     # a < b: no self-loops
+    want = S.edges_to_csr(3000, k // 3000, k % 3000, wk.numpy())
+    for a, b in zip((off, idx, w), want):
+        assert np.array_equal(a.numpy(), b)
+    valid_csr(off.numpy(), idx.numpy(), w.numpy())
+    assert wk.min() >= 1 and wk.max() <= 4
+
+
+def test_device_chung_lu_degrees_follow_the_power_law():
+    n, m = 200_000, 2_000_000
+    (off, _, _), _ = D.chung_lu(n, m, 2.1, 1, 4, seed=1, device="cpu")
+    deg = np.diff(off.numpy())
+    # expected degree ~ (i + 10)^(-1/(beta-1)): the log-log slope over the
+    # uncapped middle of the ID range is close to -1/1.1
+    i = np.array([1000, 3000, 10000, 30000, 100000])
+    d = np.array([deg[k - 100:k + 100].mean() for k in i])
+    slope = np.polyfit(np.log(i + 10.0), np.log(d), 1)[0]
+    assert -1.0 < slope < -0.8, slope
+    assert deg.max() <= int(np.sqrt(2 * m)) * 1.2            # the cap holds (up to sampling noise)
+
+
+@pytest.mark.parametrize("size", [1, 10, 1000])
+def test_device_random_batch_is_valid(size):
+    n = 5000
+    (off, idx, w), (keys, wk) = D.chung_lu(n, 20000, 2.1, 1, 4, seed=4, device="cpu")
+    dels, ins = D.random_batch(n, keys, wk, size, seed=9)
+    ni = int(round(0.8 * size))
+    assert len(ins[0]) == ni and len(dels[0]) == size - ni
+    k = keys.numpy()
+    dk = dels[0].numpy().astype(np.int64) * n + dels[1].numpy()
+    ik = ins[0].numpy().astype(np.int64) * n + ins[1].numpy()
+    assert np.all(dels[0].numpy() < dels[1].numpy()) and np.all(ins[0].numpy() < ins[1].numpy())
+    assert len(np.unique(dk)) == len(dk) and np.all(np.isin(dk, k))        # distinct existing edges
+    assert np.array_equal(dels[2].numpy(), wk.numpy()[np.searchsorted(k, dk)])  # with their weights
+    assert len(np.unique(ik)) == len(ik) and not np.any(np.isin(ik, k))    # distinct non-edges
+    assert np.all(ins[2].numpy() == 1)
