@@ -62,7 +62,9 @@ def parse():
     ap.add_argument("--sched", default="det", choices=["det", "async"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="cl", choices=["cl", "rmat", "serving", "lowdeg"])
+    ap.add_argument("--workload", default="cl", choices=["cl", "rmat", "serving", "lowdeg", "temporal"])
+    ap.add_argument("--no-temporal-extra", action="store_true",
+                    help="skip the temporal-stream figures of the default Chung-Lu line")
     ap.add_argument("--no-rmat-extra", action="store_true",
                     help="skip the compact R-MAT scale-22 figures of the default Chung-Lu line")
     ap.add_argument("--cl-div", type=int, default=1,
@@ -531,6 +533,10 @@ def run_ours(args):
                 "unit": "edges/s", **{k: rs[k] for k in ("static_ms_mean", "static_passes", "df")},
                 "roofline_frac": rs["roofline"]["frac"], "roofline_achieved": rs["roofline"]["achieved"]}
 
+    temporal = None
+    if wl.key == "cl" and not args.no_temporal_extra:
+        temporal = run_temporal_graph(args, L, dev, stream)
+
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         g, sample = wl.cpu_sample()
@@ -552,10 +558,83 @@ def run_ours(args):
         }
         if rmat is not None:
             line["rmat_s22"] = rmat
+        if temporal is not None:
+            line["temporal"] = temporal
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+TEMPORAL_N, TEMPORAL_EVENTS = 1_140_000, 7_830_000
+TEMPORAL_FRACS = (1e-5, 1e-4, 1e-3)
+TEMPORAL_SEED = 0x1EDE0 + 5
+
+
+def run_temporal_graph(args, L, dev, stream, batches_per_size=100, every=10):
+    """The temporal workload (Sec. 5.3) on a synthetic interaction stream the
+    size of wiki-talk-temporal (1.14M vertices, 7.83M events): 90% preloaded,
+    then, for each batch size of 1e-5, 1e-4 and 1e-3 |E_T| events, 100
+    consecutive insertion batches applied in turn, each followed by a DF
+    update from the previous update's membership, K and Sigma.  Every
+    ``every``-th batch also times Static, ND and DS on the same G^t.  Returns
+    the per-size figures."""
+    import torch
+    from paper_2405_11658_gb300 import synth as S
+    src, dst = S.temporal_stream(TEMPORAL_N, TEMPORAL_EVENTS, seed=TEMPORAL_SEED)
+    g0, rest = S.temporal_split(TEMPORAL_N, src, dst, 0.9)
+    opts = L.Opts(sched=L.DET if args.sched == "det" else L.ASYNC)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        b.synchronize()
+        return r, a.elapsed_time(b)
+
+    out = {}
+    cap_all = len(g0[1]) + 2 * int(round(max(TEMPORAL_FRACS) * TEMPORAL_EVENTS)) * batches_per_size + 16
+    with L.Context(max_n=TEMPORAL_N, max_nnz=cap_all, stream=stream) as ctx:
+        G0 = L.Graph.from_numpy(*g0, device=dev)
+        Cs, _ = ctx.static(G0, opts, want_q=False)
+        C0, K0, S0, _ = ctx.update(G0, Cs, None, None, "ND", opts, want_q=False)
+        for frac in TEMPORAL_FRACS:
+            size = max(1, int(round(frac * TEMPORAL_EVENTS)))
+            batches = S.temporal_batches(rest, size, batches_per_size)
+            G, C, K, Sg = G0, C0, K0, S0
+            rec = {"df": [], "static": [], "nd": [], "ds": [], "apply": [], "affected": []}
+            for k, ins in enumerate(batches):
+                iE = L.Edges.from_numpy(ins, device=dev)
+                G, t_apply = timed(lambda: ctx.apply_batch(G, None, iE, cap_nnz=cap_all))
+                (C, K, Sg, _), t_df = timed(lambda: ctx.update(G, C, None, iE, "DF", opts, prior_K=K,
+                                                               prior_Sigma=Sg, want_q=False))
+                rec["apply"].append(t_apply)
+                rec["df"].append(t_df)
+                rec["affected"].append(ctx.stats()["affected0"])
+                if k % every == every - 1:
+                    _, t = timed(lambda: ctx.static(G, opts, want_q=False))
+                    rec["static"].append(t)
+                    for mode in ("ND", "DS"):
+                        _, t = timed(lambda: ctx.update(G, C, None, iE, mode, opts, prior_K=K, prior_Sigma=Sg,
+                                                        want_q=False))
+                        rec[mode.lower()].append(t)
+            q_df = ctx.modularity(G, C)
+            _, q_static = ctx.static(G, opts)
+            s50 = float(np.median(rec["static"]))
+            out[f"{frac:g}"] = {
+                "batch_events": size, "batches": len(batches),
+                "df_ms_p50": float(np.percentile(rec["df"], 50)), "df_ms_p99": float(np.percentile(rec["df"], 99)),
+                "static_ms_p50": s50, "nd_ms_p50": float(np.median(rec["nd"])),
+                "ds_ms_p50": float(np.median(rec["ds"])), "apply_ms_p50": float(np.median(rec["apply"])),
+                "df_speedup_vs_static": s50 / float(np.median(rec["df"])),
+                "nd_speedup_vs_static": s50 / float(np.median(rec["nd"])),
+                "ds_speedup_vs_static": s50 / float(np.median(rec["ds"])),
+                "df_affected0_p50": int(np.median(rec["affected"])),
+                "q_df_after_chain": q_df, "q_static_same_graph": q_static}
+    return {"graph": f"synthetic interaction stream, {TEMPORAL_N} vertices, {TEMPORAL_EVENTS} events "
+                     f"({len(g0[1]) // 2} static edges preloaded from the first 90%)",
+            "by_batch": out}
 
 
 SERVING_METRIC = "serving: DF updates/s with p50/p99 per-batch latency, many resident graphs"
@@ -828,6 +907,35 @@ def run_lowdeg(args):
     return 0
 
 
+def run_temporal(args):
+    """``--workload temporal``: the temporal figures as their own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2405_11658_gb300 as L
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    launches0 = L.kernel_launches()
+    with Clocks(0) as clk:
+        t0 = time.perf_counter()
+        res = run_temporal_graph(args, L, dev, stream)
+        wall = time.perf_counter() - t0
+    by = res["by_batch"]
+    tot_ms = sum(v["df_ms_p50"] * v["batches"] for v in by.values())
+    tot_b = sum(v["batches"] for v in by.values())
+    line = {"metric": "DF update time per temporal batch (p50/p99) vs GPU Static, same GPU",
+            "value": tot_ms / max(1, tot_b), "unit": "ms/batch (DF, p50 over sizes)", "n_gpus": 1,
+            "steps": tot_b, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "temporal: 90% preload, 100 consecutive insertion batches per size, "
+                                   "DF chained on the returned membership, K and Sigma",
+                       "graph": res["graph"], "batch_fracs_of_events": list(TEMPORAL_FRACS),
+                       "schedule": args.sched},
+            "by_batch": by, "gpu_launches": L.kernel_launches() - launches0, "clocks": clk.summary(),
+            "wall_s": wall}
+    print(json.dumps(line))
+    return 0
+
+
 def run_profile_static(args):
     """One Static Leiden (DET) on the workload's graph (``--workload cl`` or
     ``rmat``; ``--cl-div k`` takes the Chung-Lu recipe at 1/k of the vertices
@@ -876,6 +984,8 @@ def main():
         return run_serving(args)
     if args.workload == "lowdeg":
         return run_lowdeg(args)
+    if args.workload == "temporal":
+        return run_temporal(args)
     return run_ours(args)
 
 

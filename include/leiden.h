@@ -71,7 +71,10 @@ enum { LEIDEN_ND = 1, LEIDEN_DS = 2, LEIDEN_DF = 3 };
  * against the state at its start and applied together, so the result does
  * not depend on thread timing.  ASYNC: inside a class, vertices move in place
  * as soon as they decide, as in the paper's asynchronous CPU implementation
- * (Sec. 4.7); results vary with timing. */
+ * (Sec. 4.7); the class's degree tiers run from the longest rows down, and a
+ * vertex alone in its community joins another singleton only if that one has
+ * the smaller label (Lu, Halappanavar and Kalyanaraman 2015); results vary
+ * with timing. */
 enum { LEIDEN_DET = 0, LEIDEN_ASYNC = 1 };
 
 typedef struct {
@@ -99,7 +102,28 @@ typedef struct leiden_ctx leiden_ctx;
  * LEIDEN_ENOMEM, LEIDEN_ECUDA. */
 int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_t max_nnz);
 
-/* Synchronises the stream and frees the workspace.  NULL is a no-op. */
+/* Creates a context restricted to a share of the GPU's SMs: a green context
+ * (the current device's primary context with at least sm_count SMs
+ * provisioned; the driver rounds the count up to its partition granularity,
+ * 8 SMs on this architecture), a non-blocking stream inside it that the
+ * context owns, and the workspace of leiden_ctx_create.  Every kernel the
+ * context launches runs on those SMs only, and grids are sized for them; the
+ * results are the same as on the whole GPU.  This is the GPU counterpart of
+ * running the paper's implementation on fewer threads (Sec. 5.2, strong
+ * scaling).  Device memory stays shared with the primary context, so graphs
+ * allocated elsewhere on the device can be passed in.  sms_granted (HOST, may
+ * be NULL) receives the SM count provisioned.  Every call on the context makes
+ * the green context current on the calling thread for its duration.  Errors:
+ * LEIDEN_EINVAL (sm_count outside [1, SM count], sizes out of range),
+ * LEIDEN_ENOMEM, LEIDEN_ECUDA (green contexts unavailable). */
+int leiden_ctx_create_sm(leiden_ctx **out, int32_t sm_count, int64_t max_n, int64_t max_nnz,
+                         int32_t *sms_granted);
+
+/* The number of SMs the context sizes its grids for (HOST out). */
+int leiden_ctx_sm_count(leiden_ctx *ctx, int32_t *out);
+
+/* Synchronises the stream and frees the workspace (and, for a context from
+ * leiden_ctx_create_sm, its stream and green context).  NULL is a no-op. */
 void leiden_ctx_destroy(leiden_ctx *ctx);
 
 /* Static Leiden (Alg. leiden with every vertex affected and every community

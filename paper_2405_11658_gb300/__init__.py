@@ -173,6 +173,10 @@ def lib():
     L.leiden_strerror.restype = C.c_char_p
     L.leiden_ctx_create.argtypes = [P, P, i64, i64]
     L.leiden_ctx_create.restype = C.c_int
+    L.leiden_ctx_create_sm.argtypes = [P, i32, i64, i64, P]
+    L.leiden_ctx_create_sm.restype = C.c_int
+    L.leiden_ctx_sm_count.argtypes = [P, P]
+    L.leiden_ctx_sm_count.restype = C.c_int
     L.leiden_ctx_destroy.argtypes = [P]
     L.leiden_ctx_destroy.restype = None
     L.leiden_ctx_set_timing.argtypes = [P, i32]
@@ -329,12 +333,25 @@ class Context:
     """A ``leiden_ctx``: device workspace for graphs up to (max_n, max_nnz),
     bound to a CUDA stream (default: torch's current stream)."""
 
-    def __init__(self, max_n: int, max_nnz: int, stream=None):
+    def __init__(self, max_n: int, max_nnz: int, stream=None, sm_count: int | None = None):
+        """With ``sm_count`` the context runs on a share of the GPU's SMs
+        (leiden_ctx_create_sm: a green context with its own stream; ``sms``
+        holds the count provisioned)."""
         torch = _torch()
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._h = C.c_void_p()
-        _check(lib().leiden_ctx_create(C.byref(self._h), C.c_void_p(self.stream.cuda_stream),
-                                       int(max_n), int(max_nnz)), "leiden_ctx_create")
+        if sm_count is not None:
+            self.stream = None
+            got = C.c_int32()
+            _check(lib().leiden_ctx_create_sm(C.byref(self._h), int(sm_count), int(max_n), int(max_nnz),
+                                              C.byref(got)), "leiden_ctx_create_sm")
+            self.sms = got.value
+        else:
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            _check(lib().leiden_ctx_create(C.byref(self._h), C.c_void_p(self.stream.cuda_stream),
+                                           int(max_n), int(max_nnz)), "leiden_ctx_create")
+            got = C.c_int32()
+            _check(lib().leiden_ctx_sm_count(self._h, C.byref(got)), "leiden_ctx_sm_count")
+            self.sms = got.value
         self.max_n, self.max_nnz = max_n, max_nnz
 
     def close(self):
@@ -639,7 +656,7 @@ def default_opts() -> dict:
     return {name: getattr(o, name) for name, _ in o._fields_ if name != "reserved"}
 
 
-EXPORTED = ("leiden_modularity_noalloc", "leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
+EXPORTED = ("leiden_modularity_noalloc", "leiden_ctx_create_sm", "leiden_ctx_sm_count", "leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
             "leiden_update", "leiden_modularity", "leiden_apply_batch", "leiden_get_stats",
             "leiden_ctx_set_timing", "leiden_strerror", "leiden_kernel_launches", "leiden_tiers_default",
             "leiden_tiers_validate", "leiden_ctx_set_tiers", "leiden_ctx_get_tiers", "leiden_autotune",

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libleiden.so")
 
-SOURCES = ["scan.cu", "buckets.cu", "move.cu", "hub.cu", "misc.cu", "agg.cu", "dyn.cu", "api.cu", "noalloc.cu", "tune.cu", "small.cu", "batch.cu", "server.cu"]
+SOURCES = ["scan.cu", "buckets.cu", "move.cu", "hub.cu", "misc.cu", "agg.cu", "dyn.cu", "api.cu", "noalloc.cu", "tune.cu", "green.cu", "small.cu", "batch.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
                 "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]

@@ -37,6 +37,9 @@ void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); 
 
 struct leiden_ctx {
   cudaStream_t st = nullptr;
+  // a context restricted to some SMs owns a green context and its stream
+  GreenCtx green{};
+  bool owns_stream = false;
   int device = 0, sms = 152;
   int64_t max_n = 0, max_nnz = 0;
   TierTable tiers{};
@@ -86,6 +89,13 @@ struct leiden_ctx {
 };
 
 cudaStream_t lk::ctx_stream(leiden_ctx *c) { return c->st; }
+
+lk::CtxScope::CtxScope(leiden_ctx *c) {
+  if (c && c->green.cu) pushed = green_push(c->green);
+}
+lk::CtxScope::~CtxScope() {
+  if (pushed) green_pop();
+}
 
 namespace {
 
@@ -305,23 +315,29 @@ bool narrow_scores(const Run &r, const Buckets &b) {
   return b.kmax < ((int64_t)1 << 31) && (i128)b.kmax * r.two_m * pq < ((i128)1 << 62);
 }
 
-// Launch the decide kernels of every tier of colour class s.  The tiers
-// touch disjoint vertices and only read the shared state (DET) or update it
-// with atomics (ASYNC), so they run concurrently on the auxiliary streams.
+// Launch the decide kernels of every tier of colour class s.  DET: the tiers
+// touch disjoint vertices and only read the shared state, so they run
+// concurrently on the auxiliary streams.  ASYNC: the tiers run one after the
+// other on the context stream, longest rows first, each seeing the moves the
+// tiers before it committed -- on power-law graphs the high-degree vertices
+// decide first, as they do in the paper's loop over vertex IDs.
 template <typename WT, typename ST, bool REFINE, bool ASYNC>
 void decide_class(const Run &r, MoveArgs<WT> a, const Buckets &b, int s) {
   leiden_ctx *c = r.c;
   const int nt = c->tiers.ntiers;
   int used = 0;
-  cudaEventRecord(c->ev_fork, c->st);
-  for (int t = 1; t < nt; t++) {
+  const bool serial = ASYNC;
+  const bool fork = LK_AUX_STREAMS > 0 && !serial;
+  if (fork) cudaEventRecord(c->ev_fork, c->st);
+  for (int tt = 1; tt < nt; tt++) {
+    const int t = serial ? nt - tt : tt;
     const int key = s * nt + t;
     a.list = c->vlist + b.koff[key];
     a.list_n = b.koff[key + 1] - b.koff[key];
     if (a.list_n <= 0) continue;
     const int k = used % leiden_ctx::NAUX;
-    cudaStream_t st = LK_AUX_STREAMS > 0 ? c->aux[k] : c->st;
-    if (LK_AUX_STREAMS > 0 && used < leiden_ctx::NAUX) cudaStreamWaitEvent(st, c->ev_fork, 0);
+    cudaStream_t st = fork ? c->aux[k] : c->st;
+    if (fork && used < leiden_ctx::NAUX) cudaStreamWaitEvent(st, c->ev_fork, 0);
     used++;
     const Tier &T = c->tiers.t[t];
     if (T.kind == TIER_GLOBAL) {
@@ -345,7 +361,7 @@ void decide_class(const Run &r, MoveArgs<WT> a, const Buckets &b, int s) {
     }
     launch_decide<WT, ST, REFINE, ASYNC>(T, a, c->sms, st);
   }
-  for (int k = 0; LK_AUX_STREAMS > 0 && k < used && k < leiden_ctx::NAUX; k++) {
+  for (int k = 0; fork && k < used && k < leiden_ctx::NAUX; k++) {
     cudaEventRecord(c->ev_join[k], c->aux[k]);
     cudaStreamWaitEvent(c->st, c->ev_join[k], 0);
   }
@@ -760,13 +776,12 @@ const char *leiden_strerror(int code) {
   }
 }
 
-int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_t max_nnz) {
-  if (!out || max_n < 0 || max_nnz < 0 || max_n >= INT32_MAX) return LEIDEN_EINVAL;
-  *out = nullptr;
-  leiden_ctx *c = new leiden_ctx();
-  c->st = (cudaStream_t)cuda_stream;
-  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return LEIDEN_ECUDA; }
-  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+}  // extern "C"
+
+namespace {
+// Allocates the workspace of a context whose stream, device and SM count are
+// set; on failure frees what it allocated (the caller deletes c).
+int ctx_init(leiden_ctx *c, int64_t max_n, int64_t max_nnz) {
   c->max_n = max_n;
   c->max_nnz = max_nnz;
   c->tiers = default_tiers();
@@ -821,22 +836,80 @@ int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_
   if (rc != LEIDEN_OK) {
     cudaGetLastError();
     free_all(c);
-    delete c;
     return LEIDEN_ENOMEM;
   }
   cudaMemsetAsync(c->ctr, 0, CTR_COUNT * sizeof(u64), c->st);
   // the global scratch tables start (and are always left) empty
   cudaMemsetAsync(c->gkeys, 0xff, (size_t)c->gcap * sizeof(int32_t), c->st);
   cudaMemsetAsync(c->gvals, 0, (size_t)c->gcap * sizeof(u64), c->st);
-  if (sync(c)) { free_all(c); delete c; return LEIDEN_ECUDA; }
+  if (sync(c)) { free_all(c); return LEIDEN_ECUDA; }
+  return LEIDEN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int leiden_ctx_create(leiden_ctx **out, void *cuda_stream, int64_t max_n, int64_t max_nnz) {
+  if (!out || max_n < 0 || max_nnz < 0 || max_n >= INT32_MAX) return LEIDEN_EINVAL;
+  *out = nullptr;
+  leiden_ctx *c = new leiden_ctx();
+  c->st = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return LEIDEN_ECUDA; }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int rc = ctx_init(c, max_n, max_nnz);
+  if (rc) { delete c; return rc; }
   *out = c;
   return LEIDEN_OK;
 }
 
+int leiden_ctx_create_sm(leiden_ctx **out, int32_t sm_count, int64_t max_n, int64_t max_nnz,
+                         int32_t *sms_granted) {
+  if (!out || sm_count < 1 || max_n < 0 || max_nnz < 0 || max_n >= INT32_MAX) return LEIDEN_EINVAL;
+  *out = nullptr;
+  leiden_ctx *c = new leiden_ctx();
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return LEIDEN_ECUDA; }
+  int rc = green_create(c->device, sm_count, &c->green);
+  if (rc) { delete c; return rc; }
+  c->sms = c->green.sms;
+  rc = LEIDEN_ECUDA;
+  if (green_push(c->green)) {
+    // the context stream and the auxiliary streams are created while the
+    // green context is current, so every kernel runs on its SMs
+    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) == cudaSuccess) {
+      c->owns_stream = true;
+      rc = ctx_init(c, max_n, max_nnz);
+      if (rc) cudaStreamDestroy(c->st);
+    } else {
+      cudaGetLastError();
+    }
+    green_pop();
+  }
+  if (rc) {
+    green_destroy(&c->green);
+    delete c;
+    return rc;
+  }
+  if (sms_granted) *sms_granted = c->sms;
+  *out = c;
+  return LEIDEN_OK;
+}
+
+int leiden_ctx_sm_count(leiden_ctx *c, int32_t *out) {
+  if (!c || !out) return LEIDEN_EINVAL;
+  *out = c->sms;
+  return LEIDEN_OK;
+}
+
+
 void leiden_ctx_destroy(leiden_ctx *c) {
   if (!c) return;
-  cudaStreamSynchronize(c->st);
-  free_all(c);
+  {
+    CtxScope scope(c);
+    cudaStreamSynchronize(c->st);
+    free_all(c);
+    if (c->owns_stream) cudaStreamDestroy(c->st);
+  }
+  if (c->green.green) green_destroy(&c->green);
   delete c;
 }
 
@@ -860,6 +933,7 @@ int leiden_get_stats(leiden_ctx *c, leiden_run_stats *out) {
 int leiden_static(leiden_ctx *c, const leiden_csr *g, const leiden_opts *o, int32_t *membership_out,
                   double *q_out) {
   if (!c || (!membership_out && g && g->n > 0)) return LEIDEN_EINVAL;
+  CtxScope scope(c);
   const auto t0 = std::chrono::steady_clock::now();
   Run r{};
   int rc = setup_run(c, g, o, r);
@@ -899,6 +973,7 @@ int leiden_update(leiden_ctx *c, const leiden_csr *g, const int32_t *prior_membe
                   const leiden_opts *o, int32_t *membership_out, int64_t *K_out, int64_t *Sigma_out,
                   double *q_out) {
   if (!c) return LEIDEN_EINVAL;
+  CtxScope scope(c);
   const auto t0 = std::chrono::steady_clock::now();
   Run r{};
   int rc = setup_run(c, g, o, r);
@@ -993,6 +1068,7 @@ int leiden_update(leiden_ctx *c, const leiden_csr *g, const int32_t *prior_membe
 
 int leiden_modularity(leiden_ctx *c, const leiden_csr *g, const int32_t *membership, double gamma, double *q_out) {
   if (!c || !q_out) return LEIDEN_EINVAL;
+  CtxScope scope(c);
   int rc = check_graph(c, g);
   if (rc) return rc;
   if (g->n > 0 && !membership) return LEIDEN_EINVAL;
@@ -1016,6 +1092,7 @@ int leiden_modularity(leiden_ctx *c, const leiden_csr *g, const int32_t *members
 int leiden_apply_batch(leiden_ctx *c, const leiden_csr *g, const leiden_edges *del, const leiden_edges *ins,
                        int64_t *off_out, int32_t *idx_out, int32_t *w_out, int64_t cap_nnz, int64_t *nnz_out) {
   if (!c || !off_out || !nnz_out || cap_nnz < 0) return LEIDEN_EINVAL;
+  CtxScope scope(c);
   int rc = check_graph(c, g);
   if (rc) return rc;
   const int64_t nd = del ? del->count : 0, ni = ins ? ins->count : 0;

@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(256) hub_final_k(MoveArgs<WT> a, HubWork hw) {
     if (ASYNC) {
       bool ok;
       if (!REFINE) {
+        if (a.Sig[d] == Ki && a.Sig[bc] == a.K[bc] && bc > d) continue;  // minimum-label rule
         atomic_add_i64(&a.Sig[d], -Ki);
         atomic_add_i64(&a.Sig[bc], Ki);
         a.C[i] = bc;

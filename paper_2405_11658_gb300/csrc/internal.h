@@ -46,6 +46,26 @@ void tiers_to_public(const TierTable &tt, leiden_tier_table *out);
 // The stream a context is bound to.
 cudaStream_t ctx_stream(leiden_ctx *c);
 
+// green.cu: a green context (the primary context restricted to a share of the
+// SMs).  green_push makes it current on the calling thread; green_pop undoes
+// that.
+struct GreenCtx {
+  void *green = nullptr;  // CUgreenCtx
+  void *cu = nullptr;     // CUcontext of the green context
+  int sms = 0;            // SMs provisioned
+};
+int green_create(int device, int sm_count, GreenCtx *out);
+void green_destroy(GreenCtx *g);
+bool green_push(const GreenCtx &g);
+void green_pop();
+// Makes a context's green context current for the lifetime of the object
+// (nothing for a context on the whole GPU).
+struct CtxScope {
+  explicit CtxScope(leiden_ctx *c);
+  ~CtxScope();
+  bool pushed = false;
+};
+
 template <typename WT>
 struct GraphView {
   int64_t n;

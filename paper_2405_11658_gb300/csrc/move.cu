@@ -12,7 +12,8 @@
 // DET: decide kernels read a snapshot (nothing they read is written until the
 // sub-sweep's apply kernel runs) and append proposals; apply kernels commit
 // them.  ASYNC: the deciding group commits immediately with atomics, like the
-// paper's asynchronous CPU implementation (Sec. 4.7).
+// paper's asynchronous CPU implementation (Sec. 4.7), with the minimum-label
+// rule for moves between singleton communities.
 #include <limits.h>
 
 #include "common.cuh"
@@ -100,6 +101,11 @@ __device__ __forceinline__ bool commit_async(const MoveArgs<WT> &a, int32_t i, i
                                              int32_t c) {
   const int64_t Ki = a.K[i];
   if (!REFINE) {
+    // minimum-label rule for moves between singletons (Lu, Halappanavar and
+    // Kalyanaraman 2015): two singletons deciding at the same time would swap
+    // into each other's community; a singleton joins another singleton only
+    // if that one has the smaller label
+    if (a.Sig[d] == Ki && a.Sig[c] == a.K[c] && c > d) return false;
     atomic_add_i64(&a.Sig[d], -Ki);
     atomic_add_i64(&a.Sig[c], Ki);
     a.C[i] = c;

@@ -166,6 +166,7 @@ std::vector<leiden_tier_table> candidates() {
 extern "C" int leiden_autotune(leiden_ctx *ctx, const leiden_csr *g, const leiden_opts *opts, int32_t max_trials,
                                int32_t repeats, leiden_tier_table *best_out, double *best_ms) {
   if (!ctx || !g || max_trials < 1 || repeats < 1) return LEIDEN_EINVAL;
+  CtxScope scope(ctx);  // the timing events belong to the context's (green) context
   cudaStream_t st = ctx_stream(ctx);
   leiden_tier_table keep{};
   leiden_ctx_get_tiers(ctx, &keep);

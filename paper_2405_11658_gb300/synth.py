@@ -255,3 +255,89 @@ def random_batch(off, idx, w, size: int, seed: int, ins_frac: float = 0.8, weigh
     ins = ((got // n).astype(np.int32), (got % n).astype(np.int32),
            np.full(len(got), weight, np.int32))
     return dels, ins
+
+
+def temporal_stream(n: int, n_events: int, comm_size: float = 200.0, p_within: float = 0.8,
+                    p_repeat: float = 0.45, beta: float = 2.1, seed: int = 0):
+    """A timestamped stream of n_events undirected interactions (src, dst), in
+    time order, standing in for the SNAP temporal networks of Sec. 5.3 (Q&A
+    and talk-page interactions: heavy-tailed activity, groups that mostly talk
+    among themselves, many repeated pairs; |E_T| counts the repeats).
+
+    Vertex activity follows the Chung-Lu weights (i + 10)^(-1/(beta-1)) over a
+    random permutation of the IDs; vertices fall into groups of geometric size
+    (mean comm_size).  Each event repeats a uniformly chosen earlier event with
+    probability p_repeat; otherwise its source is drawn by activity and its
+    target by activity, inside the source's group with probability p_within.
+    Self-loops are redrawn.  Returns (src, dst) int32 arrays of n_events."""
+    rng = _rng(seed)
+    act = (np.arange(n, dtype=np.float64) + 10.0) ** (-1.0 / (beta - 1.0))
+    act = act[rng.permutation(n)]
+    # groups: consecutive runs of a random vertex order, geometric sizes
+    order = rng.permutation(n)
+    cuts = np.flatnonzero(rng.random(n) < 1.0 / comm_size)
+    group = np.zeros(n, np.int64)
+    group[order] = np.searchsorted(cuts, np.arange(n), side="right")
+    ng = int(group.max()) + 1
+    # per-group activity distribution: members sorted by group, prefix sums
+    byg = np.argsort(group, kind="stable")
+    gstart = np.searchsorted(group[byg], np.arange(ng + 1))
+    gcum = np.cumsum(act[byg])
+    cdf_all = np.cumsum(act)
+    cdf_all /= cdf_all[-1]
+    m = n_events
+    # fresh events: source by activity, target by activity inside the
+    # source's group (p_within) or anywhere
+    s = np.minimum(np.searchsorted(cdf_all, rng.random(m)), n - 1)
+    t = np.minimum(np.searchsorted(cdf_all, rng.random(m)), n - 1)
+    inside = rng.random(m) < p_within
+    g = group[s]
+    lo, hi = gstart[g], gstart[g + 1]
+    base = np.where(lo > 0, gcum[np.maximum(lo - 1, 0)], 0.0)
+    span = gcum[hi - 1] - base
+    pos = np.clip(np.searchsorted(gcum, base + rng.random(m) * span, side="right"), lo, hi - 1)
+    t = np.where(inside, byg[pos], t)
+    bad = s == t
+    while bad.any():
+        t[bad] = np.minimum(np.searchsorted(cdf_all, rng.random(int(bad.sum()))), n - 1)
+        bad = s == t
+    # repeats: event k copies a uniformly chosen earlier event; chains of
+    # repeats resolve to the fresh event at their root (pointer jumping)
+    rep = rng.random(m) < p_repeat
+    rep[0] = False
+    root = np.arange(m, dtype=np.int64)
+    root[rep] = np.floor(rng.random(int(rep.sum())) * np.flatnonzero(rep)).astype(np.int64)
+    while True:
+        nxt = root[root]
+        if np.array_equal(nxt, root):
+            break
+        root = nxt
+    return s[root].astype(np.int32), t[root].astype(np.int32)
+
+
+def temporal_split(n: int, src, dst, preload: float = 0.9):
+    """The paper's temporal setup (Sec. 5.3): the first ``preload`` of the
+    stream is the initial graph (repeated pairs merge, their unit weights
+    adding up), the rest is the sequence of insertions that later batches
+    take in order.  Returns (csr, (rest_src, rest_dst))."""
+    cut = int(round(preload * len(src)))
+    u = np.asarray(src[:cut], np.int64)
+    v = np.asarray(dst[:cut], np.int64)
+    a, b = np.minimum(u, v), np.maximum(u, v)
+    key, cnt = np.unique(a * n + b, return_counts=True)
+    g = edges_to_csr(n, key // n, key % n, cnt)
+    return g, (np.asarray(src[cut:], np.int32), np.asarray(dst[cut:], np.int32))
+
+
+def temporal_batches(rest, size: int, count: int):
+    """``count`` consecutive insertion batches of ``size`` stream events each
+    (unit weight; a pair that exists or repeats adds its weight), taken in
+    time order from the events after the preload."""
+    s, d = rest
+    out = []
+    for k in range(count):
+        a, b = k * size, (k + 1) * size
+        if b > len(s):
+            break
+        out.append((s[a:b].copy(), d[a:b].copy(), np.ones(size, np.int32)))
+    return out

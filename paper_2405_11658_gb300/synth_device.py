@@ -8,7 +8,8 @@ method's arithmetic.  The recipe is the one of ``synth.chung_lu`` (ball
 dropping with endpoint probabilities proportional to (i + i0)^(-1/(beta-1)),
 expected degrees capped at sqrt(2 m), deduplication, self-loops dropped,
 resampling until exactly m undirected edges, integer weights uniform in
-[wmin, wmax]); the random numbers come from a torch generator seeded with
+[wmin, wmax]); the endpoint distribution is held as an integer prefix sum, so
+sampling is exact; the random numbers come from a torch generator seeded with
 ``seed`` on the given device, so a graph is reproducible on one machine and
 torch build, but is not the same instance as ``synth.chung_lu`` draws on the
 host.  Every function also runs on ``device="cpu"`` (used by the CPU tests).
@@ -42,19 +43,23 @@ def chung_lu_edges(n: int, m: int, beta: float = 2.1, wmin: int = 1, wmax: int =
     x = (torch.arange(n, dtype=torch.float64, device=dev) + i0) ** (-1.0 / (beta - 1.0))
     deg = x * (2.0 * m / float(x.sum()))
     deg.clamp_(max=math.sqrt(2.0 * m))
-    cdf = torch.cumsum(deg, 0)
-    cdf /= cdf[-1].item()
-    del x, deg
+    # Integer weights and an integer prefix sum: a parallel floating-point
+    # scan may add in a different order from run to run, and a last-bit
+    # change moves the sampled endpoints.  Integer sums are exact, so the
+    # graph depends on the seed alone.
+    wint = torch.round(deg * float(1 << 24)).to(torch.int64).clamp_(min=1)
+    cdf = torch.cumsum(wint, 0)
+    total = int(cdf[-1])
+    del x, deg, wint
     have = torch.empty(0, dtype=torch.int64, device=dev)
     while have.numel() < m:
         need = int((m - have.numel()) * 1.1) + 16
         parts = [have]
         for s in range(0, need, _CHUNK):
             k = min(_CHUNK, need - s)
-            u = torch.searchsorted(cdf, torch.rand(k, generator=gen, dtype=torch.float64, device=dev))
-            v = torch.searchsorted(cdf, torch.rand(k, generator=gen, dtype=torch.float64, device=dev))
-            u.clamp_(max=n - 1)
-            v.clamp_(max=n - 1)
+            # endpoint i with probability wint[i] / total: the first i with cdf[i] > r
+            u = torch.searchsorted(cdf, torch.randint(0, total, (k,), generator=gen, device=dev), right=True)
+            v = torch.searchsorted(cdf, torch.randint(0, total, (k,), generator=gen, device=dev), right=True)
             keep = u != v
             a = torch.minimum(u, v)[keep]
             b = torch.maximum(u, v)[keep]

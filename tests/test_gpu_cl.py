@@ -1,8 +1,9 @@
 """The largest single-GPU workload at full size: a Chung-Lu web-graph stand-in
 with degree exponent 2.1, 5e7 vertices, 1.0e9 undirected edges (2.0e9 CSR
-entries, int64 offsets past 2^31), integer weights uniform in 1..4, generated
-on the device (paper_2405_11658_gb300/synth_device.py), in the context shape
-bench.py uses for it (room for a 1e-1 |E| batch).
+entries, int64 offsets), integer weights uniform in 1..4, generated on the
+device (paper_2405_11658_gb300/synth_device.py), in a context with room for
+the benchmark's 1e-1 |E| batch and for an insertion batch that takes G^t past
+2^31 entries.
 
 The oracle needs hours at this size, so every run is checked through the
 properties that hold at any size (tests/props_device.py, computed on the
@@ -31,9 +32,13 @@ SEED = 0x1EDE0 + 2
 FRAC = 1e-4
 
 
+BIG_INSERT = 80_000_000   # undirected insertions: 2e9 + 1.6e8 CSR entries > 2^31
+
+
 def max_nnz_for(nnz, m):
-    # room for the largest batch the benchmark applies (1e-1 |E|, 80% insertions)
-    return nnz + 2 * int(round(0.8 * 0.1 * m)) + 16
+    # room for the benchmark's largest batch (1e-1 |E|, 80% insertions) and
+    # for the insertion-only batch below
+    return nnz + 2 * max(int(round(0.8 * 0.1 * m)), BIG_INSERT) + 16
 
 
 @pytest.fixture(scope="module")
@@ -53,9 +58,17 @@ def work():
         torch.cuda.empty_cache()
 
 
+def test_the_device_generator_is_reproducible():
+    # the graph depends on the seed alone (integer sampling distribution;
+    # no floating-point reduction whose order could vary between runs)
+    a, ka = D.chung_lu(1_000_000, 10_000_000, 2.1, 1, 4, seed=SEED, device="cuda")
+    b, kb = D.chung_lu(1_000_000, 10_000_000, 2.1, 1, 4, seed=SEED, device="cuda")
+    assert all(torch.equal(x, y) for x, y in zip(a + ka, b + kb))
+
+
 def test_the_graph_is_the_configured_one(work):
     G, _, _, _ = work
-    assert G.n == N and G.nnz == 2 * M and G.nnz > 2**31
+    assert G.n == N and G.nnz == 2 * M
     assert int(G.w.min()) >= 1 and int(G.w.max()) <= 4
 
 
@@ -108,3 +121,21 @@ def test_async_static_properties_at_full_size(work):
     G, _, _, ctx = work
     memb, q = ctx.static(G, L.Opts(sched=L.ASYNC))
     PD.check_properties(G.off, G.idx, G.w, memb, q)
+
+
+def test_static_past_2_31_entries(work):
+    # an insertion-only batch takes G^t past 2^31 CSR entries: offsets and
+    # entry positions beyond the 32-bit range in every kernel
+    G, _, _, ctx = work
+    rows = PD.row_ids(G.off)
+    upper = G.idx > rows
+    keys = rows[upper].to(torch.int64) * N + G.idx[upper].to(torch.int64)   # sorted: rows are
+    del rows, upper
+    _, ins = D.random_batch(N, keys, torch.ones_like(keys, dtype=torch.int32), BIG_INSERT, seed=7, ins_frac=1.0)
+    del keys
+    Gt = ctx.apply_batch(G, None, L.Edges(*ins), cap_nnz=max_nnz_for(G.nnz, M))
+    del ins
+    assert Gt.nnz == G.nnz + 2 * BIG_INSERT and Gt.nnz > 2**31
+    memb, q = ctx.static(Gt, L.Opts())
+    assert ctx.stats()["nnz"][0] == Gt.nnz
+    PD.check_properties(Gt.off, Gt.idx, Gt.w, memb, q)

@@ -115,3 +115,22 @@ def test_device_random_batch_is_valid(size):
     assert np.array_equal(dels[2].numpy(), wk.numpy()[np.searchsorted(k, dk)])  # with their weights
     assert len(np.unique(ik)) == len(ik) and not np.any(np.isin(ik, k))    # distinct non-edges
     assert np.all(ins[2].numpy() == 1)
+
+
+def test_temporal_stream_and_split():
+    n, ne = 5000, 60000
+    s, d = S.temporal_stream(n, ne, seed=2)
+    assert len(s) == len(d) == ne and s.dtype == np.int32
+    assert np.all(s != d) and s.min() >= 0 and s.max() < n and d.max() < n
+    key = np.minimum(s, d).astype(np.int64) * n + np.maximum(s, d)
+    distinct = len(np.unique(key))
+    assert 0.35 < 1 - distinct / ne < 0.75                 # many repeated pairs, as in |E_T| vs |E|
+    s2, d2 = S.temporal_stream(n, ne, seed=2)
+    assert np.array_equal(s, s2) and np.array_equal(d, d2)   # seeded
+    g, rest = S.temporal_split(n, s, d, 0.9)
+    valid_csr(*g)
+    assert len(rest[0]) == ne - 54000
+    assert int(g[2].sum()) == 2 * 54000                   # repeats merged by adding unit weights
+    bs = S.temporal_batches(rest, 100, 7)
+    assert len(bs) == 7 and np.array_equal(bs[3][0], rest[0][300:400]) and np.all(bs[0][2] == 1)
+    assert len(S.temporal_batches(rest, 5000, 3)) == 1    # only whole batches
