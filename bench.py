@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--sched", default="det", choices=["det", "async"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="cl", choices=["cl", "rmat", "serving", "lowdeg", "temporal"])
+    ap.add_argument("--workload", default="cl",
+                    choices=["cl", "rmat", "serving", "lowdeg", "temporal", "ablation", "smscale"])
     ap.add_argument("--no-temporal-extra", action="store_true",
                     help="skip the temporal-stream figures of the default Chung-Lu line")
     ap.add_argument("--no-rmat-extra", action="store_true",
@@ -936,6 +937,155 @@ def run_temporal(args):
     return 0
 
 
+ABLATION_FRACS = (1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1)
+ABLATION_VARIANTS = (("full_refine", 1, True), ("subset_refine", 0, True), ("optimized_aggregation", 0, False))
+
+
+def _ablation_graphs():
+    from paper_2405_11658_gb300 import synth as S
+    yield "rmat-s22", S.rmat(SCALE, EDGE_FACTOR, 0.57, 0.19, 0.19, seed=RMAT_SEED)
+    yield "grid-5000", S.grid(5000, 0.05, 0.001, seed=0x1EDE0 + 3)
+
+
+def run_ablation(args):
+    """The paper's ablation of DF Leiden (Sec. 4.2-4.4 and its figure): Full
+    Refine (every community refined in the first pass), Subset Refine (only
+    the changed ones) and Optimized Aggregation (Subset Refine with the
+    size-tiered aggregation kernels; the other two aggregate every community
+    through one bucketed method), on R-MAT scale 22 and the 5000 x 5000 grid,
+    batches of 1e-7 .. 1e-1 |E| (samples per size: --lowdeg-samples).
+    Reports the DF update time and modularity per variant and batch size."""
+    import torch
+    from paper_2405_11658_gb300 import synth as S
+    torch.cuda.set_device(0)
+    import paper_2405_11658_gb300 as L
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    out = {}
+    launches0 = L.kernel_launches()
+    with Clocks(0) as clk:
+        for name, g in _ablation_graphs():
+            pairs = S.undirected_pairs(*g)
+            nedges = len(pairs[0])
+            batches = []
+            for i, frac in enumerate(ABLATION_FRACS):
+                for k in range(args.lowdeg_samples):
+                    d, ins = S.random_batch(*g, max(2, int(round(frac * nedges))), seed=3000 + 10 * i + k,
+                                            pairs=pairs)
+                    batches.append((frac, L.Edges.from_numpy(d, device=dev), L.Edges.from_numpy(ins, device=dev)))
+            max_nnz = len(g[1]) + 2 * max(b[2].count for b in batches) + 16
+            G0 = L.Graph.from_numpy(*g, device=dev)
+            res = {}
+            with L.Context(max_n=G0.n, max_nnz=max_nnz, stream=stream) as ctx:
+                Cs, _ = ctx.static(G0, L.Opts(), want_q=False)
+                C0, K0, S0, _ = ctx.update(G0, Cs, None, None, "ND", L.Opts(), want_q=False)
+                static_ms = []
+                for frac, dE, iE in batches:
+                    Gt = ctx.apply_batch(G0, dE, iE, cap_nnz=max_nnz)
+                    key = f"{frac:g}"
+                    for vname, full, uniform in ABLATION_VARIANTS:
+                        ctx.set_agg_policy(uniform)
+                        opts = L.Opts(refine_all_first_pass=full)
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        _, _, _, q = ctx.update(Gt, C0, dE, iE, "DF", opts, prior_K=K0, prior_Sigma=S0)
+                        b.record(stream)
+                        b.synchronize()
+                        st = ctx.stats()
+                        r = res.setdefault(key, {}).setdefault(vname, {"ms": [], "q": [], "agg_ms": []})
+                        r["ms"].append(a.elapsed_time(b))
+                        r["q"].append(q)
+                        r["agg_ms"].append(sum(st["t_agg_ms"]))
+                    ctx.set_agg_policy(False)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    _, qs = ctx.static(Gt, L.Opts())
+                    b.record(stream)
+                    b.synchronize()
+                    static_ms.append(a.elapsed_time(b))
+                    res[key].setdefault("static_q", []).append(qs)
+                    del Gt
+            summ = {}
+            for key, r in res.items():
+                summ[key] = {"static_q": float(np.mean(r["static_q"]))}
+                for vname, _, _ in ABLATION_VARIANTS:
+                    summ[key][vname] = {"df_ms_p50": float(np.median(r[vname]["ms"])),
+                                        "agg_ms_p50": float(np.median(r[vname]["agg_ms"])),
+                                        "q_mean": float(np.mean(r[vname]["q"]))}
+                base = summ[key]["full_refine"]["df_ms_p50"]
+                for vname, _, _ in ABLATION_VARIANTS:
+                    summ[key][vname]["relative_to_full_refine"] = summ[key][vname]["df_ms_p50"] / base
+            out[name] = {"vertices": G0.n, "csr_entries": G0.nnz, "static_ms_p50": float(np.median(static_ms)),
+                         "by_batch": summ}
+    line = {"metric": "DF update time, Full Refine / Subset Refine / Optimized Aggregation (relative)",
+            "value": float(np.mean([v["by_batch"][k]["optimized_aggregation"]["relative_to_full_refine"]
+                                    for v in out.values() for k in v["by_batch"]])),
+            "unit": "DF time of Optimized Aggregation relative to Full Refine (mean over graphs and sizes)",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "ablation: DF Leiden with Full Refine, Subset Refine, Optimized Aggregation",
+                       "batch_fracs": list(ABLATION_FRACS), "samples_per_size": args.lowdeg_samples},
+            "graphs": out, "gpu_launches": L.kernel_launches() - launches0, "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
+SMSCALE_COUNTS = (8, 16, 32, 64, 128)
+
+
+def run_smscale(args):
+    """Static and DF Leiden (1e-4 |E| batch) on R-MAT scale 22 with the
+    context restricted to 8, 16, 32, 64 and 128 SMs (green contexts) and on
+    the whole GPU: the counterpart of the paper's strong-scaling study over
+    1..64 threads (Sec. 5.2).  Times are the calls' wall times (the calls
+    synchronise), median of --steps runs; every SM count must return the same
+    membership."""
+    import torch
+    from paper_2405_11658_gb300 import synth as S
+    torch.cuda.set_device(0)
+    import paper_2405_11658_gb300 as L
+    g = RmatWorkload(args.scale).host_graph(RMAT_SEED)
+    dels, ins = S.random_batch(*g, max(2, int(round(1e-4 * len(g[1]) / 2))), seed=77)
+    G = L.Graph.from_numpy(*g)
+    dE, iE = L.Edges.from_numpy(dels), L.Edges.from_numpy(ins)
+    total = torch.cuda.get_device_properties(0).multi_processor_count
+    rows, ref_hash = [], None
+    with Clocks(0) as clk:
+        for sms in list(SMSCALE_COUNTS) + [None]:
+            kw = {"sm_count": sms} if sms else {}
+            with L.Context(max_n=G.n, max_nnz=G.nnz + 2 * iE.count + 16, **kw) as ctx:
+                Gt = ctx.apply_batch(G, dE, iE)
+                Cs, _ = ctx.static(G, L.Opts(), want_q=False)
+                C0, K0, S0, _ = ctx.update(G, Cs, None, None, "ND", L.Opts(), want_q=False)
+                st_ms, df_ms = [], []
+                for _ in range(max(1, args.steps)):
+                    m, _ = ctx.static(Gt, L.Opts(), want_q=False)
+                    st_ms.append(ctx.stats()["total_ms"])
+                    ctx.update(Gt, C0, dE, iE, "DF", L.Opts(), prior_K=K0, prior_Sigma=S0, want_q=False)
+                    df_ms.append(ctx.stats()["total_ms"])
+                h = int(torch.sum(m.to(torch.int64) * (torch.arange(G.n, device=m.device) % 65521)))
+                ref_hash = h if ref_hash is None else ref_hash
+                rows.append({"sms": ctx.sms, "static_ms": float(np.median(st_ms)), "df_ms": float(np.median(df_ms)),
+                             "same_membership": h == ref_hash})
+    base = rows[0]
+    for r in rows:
+        r["static_speedup_vs_fewest"] = base["static_ms"] / r["static_ms"]
+        r["df_speedup_vs_fewest"] = base["df_ms"] / r["df_ms"]
+    # speedup per doubling of the SM count, from the fewest to the most SMs
+    full = rows[-1]
+    dbl = np.log2(full["sms"] / base["sms"])
+    line = {"metric": "Static / DF Leiden time vs SM count (green contexts), R-MAT scale 22",
+            "value": float((base["static_ms"] / full["static_ms"]) ** (1.0 / dbl)) if dbl > 0 else None,
+            "unit": "Static speedup per doubling of the SMs", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "sm scaling", "graph": f"R-MAT scale {args.scale}, edge factor {EDGE_FACTOR}",
+                       "df_batch": "1e-4 |E|", "sm_total": total, "runs_per_point": max(1, args.steps)},
+            "points": rows,
+            "df_speedup_per_doubling": float((base["df_ms"] / full["df_ms"]) ** (1.0 / dbl)) if dbl > 0 else None,
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def run_profile_static(args):
     """One Static Leiden (DET) on the workload's graph (``--workload cl`` or
     ``rmat``; ``--cl-div k`` takes the Chung-Lu recipe at 1/k of the vertices
@@ -986,6 +1136,10 @@ def main():
         return run_lowdeg(args)
     if args.workload == "temporal":
         return run_temporal(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
+    if args.workload == "smscale":
+        return run_smscale(args)
     return run_ours(args)
 
 

@@ -464,6 +464,18 @@ int leiden_tiers_validate(const leiden_tier_table *t);
  * context keeps its table). */
 int leiden_ctx_set_tiers(leiden_ctx *ctx, const leiden_tier_table *t);
 
+/* Aggregation policy (Alg. leidenag) of the context's following runs.
+ * LEIDEN_AGG_TIERED (the default) gives each community a kernel shape sized
+ * to its total degree -- a warp with a shared-memory table, a block, or, for
+ * giant communities, fixed-size buckets spread over many blocks -- the GPU
+ * form of the paper's Optimized Aggregation (Sec. 4.4: small work units so
+ * that one large unrefined community does not hold up a worker).
+ * LEIDEN_AGG_UNIFORM sends every community through the bucketed path, one
+ * method for all sizes, for the ablation of Sec. 4.2-4.4.  The result is the
+ * same either way.  Errors: LEIDEN_EINVAL. */
+enum { LEIDEN_AGG_TIERED = 0, LEIDEN_AGG_UNIFORM = 1 };
+int leiden_ctx_set_agg_policy(leiden_ctx *ctx, int32_t policy);
+
 /* Copies the context's tier table into *out (HOST). */
 int leiden_ctx_get_tiers(leiden_ctx *ctx, leiden_tier_table *out);
 

@@ -177,6 +177,8 @@ def lib():
     L.leiden_ctx_create_sm.restype = C.c_int
     L.leiden_ctx_sm_count.argtypes = [P, P]
     L.leiden_ctx_sm_count.restype = C.c_int
+    L.leiden_ctx_set_agg_policy.argtypes = [P, i32]
+    L.leiden_ctx_set_agg_policy.restype = C.c_int
     L.leiden_ctx_destroy.argtypes = [P]
     L.leiden_ctx_destroy.restype = None
     L.leiden_ctx_set_timing.argtypes = [P, i32]
@@ -380,6 +382,11 @@ class Context:
         t = _TierTable.of(tiers) if tiers is not None else None
         _check(lib().leiden_ctx_set_tiers(self._h, C.byref(t) if t is not None else None),
                "leiden_ctx_set_tiers", self._h)
+
+    def set_agg_policy(self, uniform: bool):
+        """Aggregation through size-tiered kernels (False, the default) or one
+        bucketed multi-block method for every community (True)."""
+        _check(lib().leiden_ctx_set_agg_policy(self._h, 1 if uniform else 0), "leiden_ctx_set_agg_policy", self._h)
 
     def get_tiers(self) -> list:
         t = _TierTable()
@@ -656,7 +663,7 @@ def default_opts() -> dict:
     return {name: getattr(o, name) for name, _ in o._fields_ if name != "reserved"}
 
 
-EXPORTED = ("leiden_modularity_noalloc", "leiden_ctx_create_sm", "leiden_ctx_sm_count", "leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
+EXPORTED = ("leiden_modularity_noalloc", "leiden_ctx_set_agg_policy", "leiden_ctx_create_sm", "leiden_ctx_sm_count", "leiden_ctx_last_error", "leiden_opts_default", "leiden_ctx_create", "leiden_ctx_destroy", "leiden_static",
             "leiden_update", "leiden_modularity", "leiden_apply_batch", "leiden_get_stats",
             "leiden_ctx_set_timing", "leiden_strerror", "leiden_kernel_launches", "leiden_tiers_default",
             "leiden_tiers_validate", "leiden_ctx_set_tiers", "leiden_ctx_get_tiers", "leiden_autotune",

@@ -637,13 +637,21 @@ __global__ void agg_compact_win_k(const int32_t *list, int64_t nlist, const int6
   }
 }
 
-static TierTable agg_tiers() {
+// Communities by total degree: a warp with a small or a larger shared table,
+// a block, or the bucketed multi-block path for giant ones -- the GPU form of
+// the paper's Optimized Aggregation (Sec. 4.4), which keeps one large
+// unrefined community from holding up a worker.  uniform = 1 sends every
+// community through the multi-block path instead (one method for all sizes,
+// for the ablation of that design).
+static TierTable agg_tiers(int uniform) {
   TierTable tt{};
   int k = 0;
   tt.t[k++] = {TIER_SKIP, 0, 0, 0, 0};
-  tt.t[k++] = {TIER_GROUP, 48, 32, 7, 256};     // warp, 128 slots
-  tt.t[k++] = {TIER_GROUP, 384, 32, 10, 128};   // warp, 1024 slots
-  tt.t[k++] = {TIER_BLOCK, 2048, 0, 12, 256};   // block, 4096 slots (48 KB: 4 blocks per SM)
+  if (!uniform) {
+    tt.t[k++] = {TIER_GROUP, 48, 32, 7, 256};     // warp, 128 slots
+    tt.t[k++] = {TIER_GROUP, 384, 32, 10, 128};   // warp, 1024 slots
+    tt.t[k++] = {TIER_BLOCK, 2048, 0, 12, 256};   // block, 4096 slots (48 KB: 4 blocks per SM)
+  }
   tt.t[k++] = {TIER_GLOBAL, INT64_MAX, 0, 0, 256};
   tt.ntiers = k;
   return tt;
@@ -662,7 +670,7 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
   exclusive_scan<int64_t>(wk.ctdeg, wk.hoff, nc, wk.scan_tmp, s);
   if (n > 0) LK_COUNTED agg_place_k<<<gridn(n, 256), 256, 0, s>>>(n, C, wk.coff, wk.ccur, wk.cv);
 
-  const TierTable tt = agg_tiers();
+  const TierTable tt = agg_tiers(wk.uniform);
   launch_buckets(wk.hoff, nc, 0, tt, wk.clist, wk.blockhist, wk.scanned, wk.koff_dev, wk.scan_tmp, s);
   cudaMemcpyAsync(wk.h_koff, wk.koff_dev, (size_t)(tt.ntiers + 1) * sizeof(int64_t),
                   cudaMemcpyDeviceToHost, s);

@@ -43,6 +43,7 @@ struct leiden_ctx {
   int device = 0, sms = 152;
   int64_t max_n = 0, max_nnz = 0;
   TierTable tiers{};
+  int agg_uniform = 0;   // aggregation policy (leiden_ctx_set_agg_policy)
   std::vector<void *> allocs;
   int64_t device_bytes = 0;
   // vertex arrays
@@ -484,6 +485,7 @@ AggWork agg_work(leiden_ctx *c) {
   w.blockhist = c->blockhist; w.scanned = c->scanned; w.koff_dev = c->koff_dev; w.scan_tmp = c->scan_tmp;
   w.h_koff = c->h_koff; w.Kout = c->Kp; w.ctr = c->ctr; w.sms = c->sms;
   w.bcnt = c->bcnt; w.bpos = c->bpos; w.bcap = c->bcap;
+  w.uniform = c->agg_uniform;
   return w;
 }
 
@@ -747,6 +749,12 @@ int leiden_ctx_set_tiers(leiden_ctx *c, const leiden_tier_table *t) {
   TierTable tt;
   if (tiers_from_public(t, &tt) != LEIDEN_OK) return LEIDEN_EINVAL;
   c->tiers = tt;
+  return LEIDEN_OK;
+}
+
+int leiden_ctx_set_agg_policy(leiden_ctx *c, int32_t policy) {
+  if (!c || (policy != LEIDEN_AGG_TIERED && policy != LEIDEN_AGG_UNIFORM)) return LEIDEN_EINVAL;
+  c->agg_uniform = policy == LEIDEN_AGG_UNIFORM;
   return LEIDEN_OK;
 }
 

@@ -268,6 +268,7 @@ struct AggWork {
   int64_t bcap;
   u64 *ctr;
   int sms;
+  int uniform;           // 1: every community through the multi-block path
 };
 template <typename WT>
 int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int32_t *idx2,

@@ -378,12 +378,14 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
   __shared__ int64_t r_kid[32];
   __shared__ int32_t s_mv;
   __shared__ unsigned s_nused;
-  __shared__ u64 wscratch[32][32];
   typedef typename TableVal<ST>::type VT;
   const int Hmax = 1 << log2H;
   VT *vals = reinterpret_cast<VT *>(smem);
   int32_t *keys = reinterpret_cast<int32_t *>(vals + Hmax);
   uint16_t *used = reinterpret_cast<uint16_t *>(keys + Hmax);   // Hmax / 2 entries
+  // the warps' combine scratch follows, 32 words per warp of this block (sized
+  // by the launch, so small blocks keep their shared memory small)
+  u64 (*wscratch)[32] = reinterpret_cast<u64 (*)[32]>(used + Hmax / 2);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   int64_t scanned = 0, nvert = 0, ncand = 0, nmoves = 0;
   i128 accS = 0;
@@ -656,9 +658,10 @@ void launch_decide(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s
   }
   if (t.kind != TIER_BLOCK) return;  // hub rows go through launch_hubs
   const int log2H = t.log2H;
-  // table (value, key) plus the list of used slots (at most half the table)
+  // table (value, key), the list of used slots (at most half the table) and
+  // the warps' combine scratch
   const size_t smem = (size_t)(1u << log2H) * (sizeof(typename TableVal<ST>::type) + sizeof(int32_t)) +
-                      (size_t)(1u << log2H);
+                      (size_t)(1u << log2H) + (size_t)(t.threads / 32) * 32 * sizeof(u64);
   int64_t blocks = a.list_n;
   const int64_t cap = (int64_t)sms * 8;
   if (blocks > cap) blocks = cap;

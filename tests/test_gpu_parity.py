@@ -134,6 +134,27 @@ def test_score_width_per_level_is_bit_exact(ctx, gamma):
     assert not st["wide_passes"] & 1 and st["wide_passes"] >> 1, st["wide_passes"]
 
 
+@pytest.mark.parametrize("name", ["pp_1e4", "rmat14", "grid", "hubs", "chung_lu_w"])
+def test_uniform_aggregation_gives_the_same_result(ctx, name):
+    # the ablation's aggregation policy (every community through the bucketed
+    # multi-block path) changes the kernels, not the super-vertex graph
+    g = GRAPHS[name]()
+    ref = O.static(*g, O.LeidenOpts())
+    ctx.set_agg_policy(True)
+    try:
+        memb, q, st = run_static(ctx, g, L.Opts())
+        dels, ins = S.random_batch(*g, 40, seed=2)
+        gt = O.apply_batch(*g, dels, ins)
+        ref2 = O.update(*gt, ref.membership, None, None, dels, ins, "DF")
+        m2, _, _, q2 = ctx.update(L.Graph.from_numpy(*gt), torch.from_numpy(ref.membership).cuda(),
+                                  L.Edges.from_numpy(dels), L.Edges.from_numpy(ins), "DF")
+    finally:
+        ctx.set_agg_policy(False)
+    assert np.array_equal(memb, ref.membership) and q == ref.q
+    assert_stats_equal(st, ref.stats)
+    assert np.array_equal(m2.cpu().numpy(), ref2.membership) and q2 == ref2.q
+
+
 def test_static_max_passes_and_iters(ctx):
     g = S.planted_partition(3000, 6, 0.02, 0.002, 5)
     for mp, mi in ((1, 20), (2, 3), (10, 1)):
