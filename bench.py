@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default="cl",
                     choices=["cl", "rmat", "serving", "lowdeg", "temporal", "ablation", "smscale"])
+    ap.add_argument("--no-serving-extra", action="store_true",
+                    help="skip the compact serving figures of the default Chung-Lu line")
     ap.add_argument("--no-temporal-extra", action="store_true",
                     help="skip the temporal-stream figures of the default Chung-Lu line")
     ap.add_argument("--no-rmat-extra", action="store_true",
@@ -426,6 +428,12 @@ def run_graph(args, wl, L, dev, stream, rank, world, steps, warmup, e2e_steps, w
         idx_h = torch.from_numpy(host[1]).pin_memory()
         w_h = torch.from_numpy(host[2]).pin_memory()
         m_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        # pinned host copies of a few batches for the DF end-to-end leg
+        host_batches = []
+        for frac in sorted({b[0] for b in batches})[:2]:
+            _, dE, iE = next(b for b in batches if b[0] == frac)
+            host_batches.append((frac, tuple(x.cpu().pin_memory() for x in (dE.src, dE.dst, dE.w)),
+                                 tuple(x.cpu().pin_memory() for x in (iE.src, iE.dst, iE.w))))
         del G0, batches
         torch.cuda.empty_cache()
         Gd = L.Graph(torch.empty_like(off_h, device=dev), torch.empty_like(idx_h, device=dev),
@@ -451,6 +459,34 @@ def run_graph(args, wl, L, dev, stream, rank, world, steps, warmup, e2e_steps, w
         out["e2e"] = {"value": e_edges / (e_ms / 1000.0), "unit": "edges/s",
                       "h2d_bytes_per_step": int(off_h.nbytes + idx_h.nbytes + w_h.nbytes),
                       "d2h_bytes_per_step": int(n * 4)}
+        # DF end to end: the batch copied in from pinned host memory, G^t built,
+        # the DF update from the base membership, the membership copied out
+        Gd.off.copy_(off_h)
+        Gd.idx.copy_(idx_h)
+        Gd.w.copy_(w_h)
+        torch.cuda.synchronize()
+        df_e2e = {}
+        for k in range(e2e_steps + 1):
+            frac, dE, iE = host_batches[k % len(host_batches)]
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            dD = L.Edges(*(x.to(dev, non_blocking=True) for x in dE))
+            iD = L.Edges(*(x.to(dev, non_blocking=True) for x in iE))
+            Gt = ctx.apply_batch(Gd, dD, iD, cap_nnz=max_nnz)
+            ctx.update(Gt, C0, dD, iD, "DF", opts, prior_K=K0, prior_Sigma=S0, out=mdev, want_q=False)
+            m_h.copy_(mdev, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            del Gt
+            if k > 0:
+                r = df_e2e.setdefault(f"{frac:g}", {"ms": [], "h2d": 0})
+                r["ms"].append(a.elapsed_time(b))
+                r["h2d"] = int(sum(x.nbytes for x in dE) + sum(x.nbytes for x in iE))
+        out["e2e_df"] = {key: {"ms_p50": float(np.median(v["ms"])), "samples": len(v["ms"]),
+                               "h2d_bytes_per_update": v["h2d"], "d2h_bytes_per_update": int(n * 4)}
+                         for key, v in df_e2e.items()}
         del Gd, off_h, idx_h, w_h
     ctx.close()
     torch.cuda.empty_cache()
@@ -537,6 +573,9 @@ def run_ours(args):
     temporal = None
     if wl.key == "cl" and not args.no_temporal_extra:
         temporal = run_temporal_graph(args, L, dev, stream)
+    serving = None
+    if wl.key == "cl" and not args.no_serving_extra:
+        serving = run_serving_compact(L)
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -553,6 +592,7 @@ def run_ours(args):
             "roofline": summ["roofline"],
             "cpu_baseline": base,
             "e2e": out.get("e2e"),
+            "e2e_df": out.get("e2e_df"),
             "gpu_launches": launches,
             "clocks": out["clocks"],
             "wall_s": out["wall"],
@@ -561,6 +601,8 @@ def run_ours(args):
             line["rmat_s22"] = rmat
         if temporal is not None:
             line["temporal"] = temporal
+        if serving is not None:
+            line["serving"] = serving
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -636,6 +678,99 @@ def run_temporal_graph(args, L, dev, stream, batches_per_size=100, every=10):
     return {"graph": f"synthetic interaction stream, {TEMPORAL_N} vertices, {TEMPORAL_EVENTS} events "
                      f"({len(g0[1]) // 2} static edges preloaded from the first 90%)",
             "by_batch": out}
+
+
+def _compact_serving_graph(k):
+    """Graph k of the compact serving mix: 16 small planted-partition graphs
+    (1e4..3e4 vertices, mean degree ~8: inside the persistent path's limits)
+    and 8 larger R-MAT graphs (scale 16..20, edge factor 8..16), each with a
+    stream of 12 update batches of 1e-6..1e-3 |E| (80/20, valid in any order)."""
+    from paper_2405_11658_gb300 import synth as S
+    rng = np.random.default_rng(0x5E7 + k)
+    if k < 16:
+        n = int(10 ** rng.uniform(4.0, np.log10(3e4)))
+        comms = max(4, n // 400)
+        g = S.planted_partition(n, comms, 7.0 / (n / comms), 1.0 / n, 0x5E70 + k)
+        kind = "pp"
+    else:
+        scale = 16 + (k - 16) % 5
+        g = S.rmat(scale, 8 if k % 2 else 16, 0.57, 0.19, 0.19, seed=0x5E70 + k)
+        kind = f"rmat{scale}"
+    off, idx, w = g
+    n = len(off) - 1
+    eu, ev, ew = S.undirected_pairs(off, idx, w)
+    keys = np.sort(eu * n + ev)
+    perm = rng.permutation(len(eu))
+    used, stream = 0, []
+    for _ in range(12):
+        size = max(2, int(round(10 ** rng.uniform(-6, -3) * len(eu))))
+        nd = size // 5
+        pick = perm[used:used + nd]
+        used += nd
+        dels = (eu[pick].astype(np.int32), ev[pick].astype(np.int32), ew[pick].astype(np.int32))
+        a = rng.integers(0, n, size=2 * size + 16)
+        b = rng.integers(0, n, size=2 * size + 16)
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        cand = lo * n + hi
+        pos = np.minimum(np.searchsorted(keys, cand), len(keys) - 1)
+        cand = np.unique(cand[(lo != hi) & (keys[pos] != cand)])[:size - nd]
+        ins = ((cand // n).astype(np.int32), (cand % n).astype(np.int32), np.ones(len(cand), np.int32))
+        stream.append((dels, ins))
+    return kind, g, stream
+
+
+def run_serving_compact(L):
+    """A compact serving run for the default line: 24 resident graphs; update
+    batches arrive in bursts (exponential gaps) that each bring one batch for
+    every small graph and one for two of the large ones, so requests arrive
+    while others run, small graphs are batched into persistent launches and
+    large ones overlap on the large-graph workers.  Returns updates/s, p50/p99
+    latency overall and per path, and graphs per persistent launch."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1)) as pool:
+        work = pool.map(_compact_serving_graph, range(24), chunksize=1)
+    rng = np.random.default_rng(11)
+    cfg = dict(hbm_budget=40 << 30, large_slots=2, small_max_graphs=32,
+               large_max_n=max(len(g[0]) for _, g, _ in work),
+               large_max_nnz=int(max(len(g[1]) for _, g, _ in work) * 1.2) + 4096,
+               small_max_n=1 << 16, small_max_nnz=1 << 18, small_batch_n=1 << 21, small_batch_nnz=1 << 24,
+               growth=0.05, small_workers=1, min_persistent=4)
+    with L.Server(**cfg) as srv:
+        ids = []
+        for _, g, _ in work:
+            gid, rid = srv.admit(*g)
+            srv.wait(rid)
+            ids.append(gid)
+        small = [k for k, (kind, _, _) in enumerate(work) if kind == "pp"]
+        large = [k for k in range(len(work)) if k not in small]
+        nxt = [0] * len(work)
+        submitted = []
+        t0 = time.perf_counter()
+        for burst in range(12):
+            time.sleep(rng.exponential(0.05))
+            for k in small + list(rng.choice(large, size=2, replace=False)):
+                if nxt[k] < len(work[k][2]):
+                    dels, ins = work[k][2][nxt[k]]
+                    nxt[k] += 1
+                    submitted.append(srv.submit(ids[k], dels, ins))
+        infos = [srv.wait(r) for r in submitted]
+        t1 = time.perf_counter()
+        st = srv.stats()
+    ok = [x for x in infos if x["status"] == 0]
+    lat = np.array([x["latency_ms"] for x in ok])
+    per_path = {}
+    for path, name in ((0, "persistent"), (1, "large"), (2, "small_alone")):
+        v = np.array([x["latency_ms"] for x in ok if x["path"] == path])
+        if len(v):
+            per_path[name] = {"requests": int(len(v)), "p50_ms": float(np.percentile(v, 50)),
+                              "p99_ms": float(np.percentile(v, 99))}
+    sizes = [x["launch_graphs"] for x in ok if x["path"] == 0]
+    return {"workload": "24 resident graphs (16 planted partitions of 1e4..3e4 vertices, 8 R-MAT of "
+                        "scale 16..20), 12 bursts of DF update batches of 1e-6..1e-3 |E|",
+            "updates_per_s": len(ok) / (t1 - t0), "requests": len(infos), "failed": len(infos) - len(ok),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "paths": per_path, "mean_graphs_per_persistent_launch": float(np.mean(sizes)) if sizes else None,
+            "persistent_launches": st.get("small_launches")}
 
 
 SERVING_METRIC = "serving: DF updates/s with p50/p99 per-batch latency, many resident graphs"

@@ -438,9 +438,11 @@ uint64_t leiden_kernel_launches(void);
 enum { LEIDEN_TIER_GROUP = 1, LEIDEN_TIER_BLOCK = 2, LEIDEN_TIER_HUB = 3 };
 typedef struct {
   int32_t kind;        /* LEIDEN_TIER_GROUP, LEIDEN_TIER_BLOCK or LEIDEN_TIER_HUB */
-  int32_t lanes;       /* GROUP: lanes per vertex, 4, 8, 16 or 32; otherwise 0 */
-  int32_t log2_slots;  /* GROUP: (lanes, log2_slots) in (4,3) (4,4) (8,4) (8,5) (16,5) (16,6)
-                        * (32,6..10); BLOCK: 6..14; HUB: 0 */
+  int32_t lanes;       /* GROUP: lanes per vertex, 1, 4, 8, 16 or 32; otherwise 0 */
+  int32_t log2_slots;  /* GROUP: (lanes, log2_slots) in (1,2) (1,3) (4,3) (4,4) (8,4) (8,5) (16,5)
+                        * (16,6) (32,6..10); with 1 lane the row is held in 2^log2_slots
+                        * registers (max_degree <= 2^log2_slots) instead of a table;
+                        * BLOCK: 6..14; HUB: 0 */
   int32_t threads;     /* GROUP: 32..256, BLOCK: 64..1024, multiples of 32; HUB: 0 */
   int64_t max_degree;  /* inclusive upper end of the degree range; HUB: ignored */
 } leiden_tier;
@@ -455,8 +457,9 @@ void leiden_tiers_default(leiden_tier_table *out);
 
 /* Checks a tier table (HOST, no GPU needed): kinds and shapes from the lists
  * above, max_degree increasing, 2^log2_slots >= 2 * max_degree for GROUP and
- * BLOCK tiers (a table never fills past half), shared memory within 227 KB
- * per block, exactly one HUB tier, last.  Returns LEIDEN_OK or LEIDEN_EINVAL. */
+ * BLOCK tiers (a table never fills past half; >= max_degree for a one-lane
+ * GROUP tier), shared memory within 227 KB per block, exactly one HUB tier,
+ * last.  Returns LEIDEN_OK or LEIDEN_EINVAL. */
 int leiden_tiers_validate(const leiden_tier_table *t);
 
 /* Sets the context's tier table (HOST; NULL restores the default) for its

@@ -1107,22 +1107,32 @@ int leiden_apply_batch(leiden_ctx *c, const leiden_csr *g, const leiden_edges *d
   if (nd < 0 || ni < 0) return LEIDEN_EINVAL;
   if ((nd > 0 && (!del->src || !del->dst || !del->w)) || (ni > 0 && (!ins->src || !ins->dst || !ins->w)))
     return LEIDEN_EINVAL;
-  if (2 * ni > c->max_nnz) return LEIDEN_ENOMEM;
+  if (2 * (ni + nd) > c->max_nnz) return LEIDEN_ENOMEM;
   if (cap_nnz > 0 && (!idx_out || !w_out)) return LEIDEN_EINVAL;
   rc = validate_graph(c, g);
   if (rc) return rc;
+  // scratch borrowed from the workspace (all free outside a Leiden run)
+  const int64_t U = 2 * (ni + nd);
   BatchWork w{};
-  w.cnt = c->ccount; w.ioff = c->coff; w.cur = c->ccur;
-  w.idst = c->hidx; w.iwt = reinterpret_cast<int32_t *>(c->hw);
+  w.cnt = c->ccount; w.uoff = c->coff; w.cur = c->ccur;
+  w.ut = c->hidx;
+  w.uw = reinterpret_cast<int32_t *>(c->hw);
+  w.Rp = reinterpret_cast<int32_t *>(c->hw) + c->max_nnz;
+  w.Np = c->gidx[0];
+  uint8_t *scratch = reinterpret_cast<uint8_t *>(c->gvals);    // 8 * gcap >= U + nnz / 8 + 16 bytes
+  w.uk = scratch;
+  w.bits = reinterpret_cast<uint32_t *>(scratch + ((U + 15) & ~(int64_t)15));
+  w.tflag = c->flag; w.tpos = c->cdist; w.trow = c->cv;
   w.newdeg = c->ctdeg;
-  w.delmark = reinterpret_cast<uint8_t *>(c->gvals);
   w.scan_tmp = c->scan_tmp;
   w.err = &c->ctr[CTR_ERROR];
   rc = apply_batch(g->n, g->off, g->idx, g->w, nd, nd ? del->src : nullptr, nd ? del->dst : nullptr,
                    nd ? del->w : nullptr, ni, ni ? ins->src : nullptr, ni ? ins->dst : nullptr,
                    ni ? ins->w : nullptr, off_out, idx_out, w_out, cap_nnz, nnz_out, w, c->st);
-  // the deletion marks borrowed the scratch values: leave them zero again
-  if (g->nnz > 0) cudaMemsetAsync(c->gvals, 0, (size_t)g->nnz, c->st);
+  // the record kinds and the row-start bits borrowed the scratch values:
+  // leave them zero again
+  const int64_t used = ((U + 15) & ~(int64_t)15) + ((g->nnz + 31) / 32 + 1) * 4;
+  cudaMemsetAsync(c->gvals, 0, (size_t)used, c->st);
   const int rc2 = sync(c);
   return rc ? rc : rc2;
 }

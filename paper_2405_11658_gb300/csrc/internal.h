@@ -291,15 +291,18 @@ void launch_mark_ds(int64_t n, const int64_t *off, const int32_t *idx, const int
                     uint8_t *affected, const DsWork &wk, cudaStream_t s);
 
 struct BatchWork {
-  int64_t *cnt;      // [n+1] insert counts per row, then offsets
-  int64_t *ioff;     // [n+1]
-  int64_t *cur;      // [n]
-  int32_t *idst;     // [2*ni]
-  int32_t *iwt;      // [2*ni]
-  int32_t *imatch;   // [2*ni] entry index of an existing edge, or -1
+  int64_t *cnt;      // [n+1] updates per row, then merged records per touched row
+  int64_t *uoff;     // [n+1] exclusive scan of the update counts
+  int64_t *cur;      // [n+1]
+  int32_t *ut;       // [2*(nd+ni)] update targets, by row
+  int32_t *uw;       // [2*(nd+ni)] signed weights (deletions negative), then new weights
+  uint8_t *uk;       // [2*(nd+ni)] record kinds
+  int32_t *Rp, *Np;  // [2*(nd+ni)] removed / new entries before each record of its row
+  uint8_t *tflag;    // [n+1] touched rows
+  int64_t *tpos;     // [n+1] their exclusive scan
+  int32_t *trow;     // [n] touched rows in increasing order
   int64_t *newdeg;   // [n+1]
-  uint8_t *delmark;  // [nnz]
-  int32_t *wadd;     // [nnz] merged insertion weight per existing entry
+  uint32_t *bits;    // [nnz/32 + 1] row starts
   int64_t *scan_tmp;
   u64 *err;
 };

@@ -328,6 +328,132 @@ __global__ void LK_GROUP_BOUNDS decide_group(MoveArgs<WT> a) {
 }
 
 // ---------------------------------------------------------------------------
+// Thread tier: one lane per vertex, for rows of at most KMAX entries.  The
+// row's neighbours, weights and communities are loaded into registers with
+// all of the row's loads in flight at once, equal communities are merged in
+// registers (the first occurrence keeps the sum), and the candidates' Sigma'
+// are gathered together: no table, no cooperation between lanes, 32 vertices
+// per warp instead of 32 / G.  The decision is the one of the other tiers
+// (same scores, same tie-break).
+// ---------------------------------------------------------------------------
+template <int KMAX, bool REFINE, bool ASYNC, typename WT, typename ST>
+__global__ void __launch_bounds__(256) decide_thread(MoveArgs<WT> a) {
+  int64_t scanned = 0, nvert = 0, ncand = 0, nmoves = 0;
+  i128 accS = 0;
+  const int lane = threadIdx.x & 31;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform loop (the proposal reservation needs the whole warp)
+  for (int64_t base = gt - lane; base < a.list_n; base += nt) {
+    const int64_t li = base + lane;
+    const bool valid = li < a.list_n;
+    const int32_t i = valid ? a.list[li] : 0;
+    int64_t e0 = 0, e1 = 0, Ki = 0, Sd = 0;
+    int32_t d = 0;
+    if (a.spec && valid) {
+      e0 = a.g.off[i];
+      e1 = a.g.off[i + 1];
+      d = a.C[i];
+      Ki = a.K[i];
+      if (!ASYNC) Sd = a.Sig[d];
+    }
+    const bool act = valid && eligible<REFINE>(a, i);
+    if (!a.spec && act) {
+      e0 = a.g.off[i];
+      e1 = a.g.off[i + 1];
+      d = a.C[i];
+      Ki = a.K[i];
+      if (!ASYNC) Sd = a.Sig[d];
+    }
+    const int deg = act ? (int)(e1 - e0) : 0;  // at most KMAX by the tier
+    const int32_t cbi = (REFINE && act) ? a.CB[i] : 0;
+    int32_t cc[KMAX];
+    int64_t ww[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; k++) {
+      cc[k] = k < deg ? a.g.idx[e0 + k] : -1;
+      ww[k] = k < deg ? (int64_t)a.g.w[e0 + k] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < KMAX; k++) {
+      const int32_t j = cc[k];
+      bool ok = j >= 0 && j != i;                          // self = false
+      if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
+      if (REFINE && ok && a.CB[j] != cbi) ok = false;      // scanBounded
+      cc[k] = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
+    }
+    // merge equal communities into their first occurrence
+#pragma unroll
+    for (int k = 1; k < KMAX; k++) {
+#pragma unroll
+      for (int k2 = 0; k2 < k; k2++)
+        if (cc[k] != LEIDEN_EMPTY_KEY && cc[k2] == cc[k]) {
+          ww[k2] += ww[k];
+          cc[k] = LEIDEN_EMPTY_KEY;
+        }
+    }
+    int64_t sg[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; k++) sg[k] = (cc[k] != LEIDEN_EMPTY_KEY && cc[k] != d) ? a.Sig[cc[k]] : 0;
+    const ST A = (ST)a.A;
+    const ST B = (ST)a.p * (ST)Ki;
+    ST bsc = 0;
+    int32_t bc = INT32_MAX;
+    int64_t kid = 0;
+#pragma unroll
+    for (int k = 0; k < KMAX; k++) {
+      const int32_t c = cc[k];
+      if (c == LEIDEN_EMPTY_KEY) continue;
+      ncand++;
+      if (c == d) { kid = ww[k]; continue; }
+      const ST sc = A * (ST)ww[k] - B * (ST)sg[k];
+      if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
+    }
+    if (act) { scanned += deg; nvert++; }
+    bool propose = false;
+    i128 S = 0;
+    if (act && bc != INT32_MAX) {
+      S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - (ASYNC ? a.Sig[d] : Sd));
+      propose = S > 0;                                     // strictly better only
+      if (REFINE && propose && a.C[bc] != bc) propose = false;  // target's vertex left
+    }
+    if (ASYNC) {
+      if (propose) {
+        propose = commit_async<REFINE>(a, i, d, bc);
+        if (propose) { accS += S; nmoves++; }
+      }
+      if (!REFINE && propose)
+        for (int64_t e = e0; e < e1; e++) a.processed[a.g.idx[e]] = 0;
+    } else {
+      const u64 slot = warp_reserve(a.prop_count, propose);
+      if (propose) {
+        a.prop_i[slot] = i;
+        a.prop_c[slot] = bc;
+        a.prop_S[slot] = S;
+        if (REFINE) a.stamp[i] = a.stamp_val;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    scanned += shfl_xor_i64(scanned, o);
+    nvert += shfl_xor_i64(nvert, o);
+    ncand += shfl_xor_i64(ncand, o);
+    nmoves += shfl_xor_i64(nmoves, o);
+    if (ASYNC) accS += shfl_xor_i128(accS, o);
+  }
+  if (lane == 0) {
+    if (scanned) atomicAdd(&a.ctr[CTR_SCANNED_ENTRIES], (u64)scanned);
+    if (nvert) atomicAdd(&a.ctr[CTR_SCANNED_VERTICES], (u64)nvert);
+    if (ncand) atomicAdd(&a.ctr[CTR_CANDIDATES], (u64)ncand);
+    if (ASYNC && nmoves) {
+      atomicAdd(&a.ctr[CTR_MOVES], (u64)nmoves);
+      atomic_add_i128(&a.ctr[CTR_SUMS_LO], accS);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Block tiers: one block per vertex, table in shared memory.  The table is
 // cleared once per block; each vertex lists the slots it occupies and the
 // scan resets exactly those while reading them, so a vertex costs work in
@@ -645,6 +771,16 @@ void launch_decide(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s
     launch_decide<WT, ST, REFINE, ASYNC>(b, a, sms, s);
     return;
   }
+  if (t.kind == TIER_GROUP && t.G == 1) {
+    // one lane per vertex; log2H holds the register capacity, 4 or 8 entries
+    int64_t blocks = (a.list_n + t.threads - 1) / t.threads;
+    const int64_t cap = (int64_t)sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (t.log2H == 2) LK_COUNTED decide_thread<4, REFINE, ASYNC, WT, ST><<<(unsigned)blocks, t.threads, 0, s>>>(a);
+    else if (t.log2H == 3) LK_COUNTED decide_thread<8, REFINE, ASYNC, WT, ST><<<(unsigned)blocks, t.threads, 0, s>>>(a);
+    return;
+  }
   if (t.kind == TIER_GROUP) {
 #define LK_GROUP(GG, LH)                                                        \
   if (t.G == GG && t.log2H == LH) {                                             \
@@ -685,8 +821,9 @@ TierTable default_tiers() {
   TierTable tt{};
   int k = 0;
   tt.t[k++] = {TIER_SKIP, 0, 0, 0, 0};
-  tt.t[k++] = {TIER_GROUP, 4, 4, 3, 256};
-  tt.t[k++] = {TIER_GROUP, 8, 8, 4, 256};
+  // rows of up to 8 entries: one lane per vertex, the row in registers
+  tt.t[k++] = {TIER_GROUP, 4, 1, 2, 256};
+  tt.t[k++] = {TIER_GROUP, 8, 1, 3, 256};
   tt.t[k++] = {TIER_GROUP, 16, 16, 5, 256};
   tt.t[k++] = {TIER_GROUP, 32, 32, 6, 256};
   tt.t[k++] = {TIER_GROUP, 128, 32, 8, 256};

@@ -25,6 +25,7 @@ constexpr int64_t kBlockStaticSmem = 10 * 1024;    // decide_block's scratch, ro
 
 bool group_shape_supported(int lanes, int log2_slots) {
   switch (lanes) {
+    case 1: return log2_slots == 2 || log2_slots == 3;   // one lane, 4 or 8 entries in registers
     case 4: return log2_slots == 3 || log2_slots == 4;
     case 8: return log2_slots == 4 || log2_slots == 5;
     case 16: return log2_slots == 5 || log2_slots == 6;
@@ -98,8 +99,13 @@ extern "C" int leiden_tiers_validate(const leiden_tier_table *t) {
     } else {
       return LEIDEN_EINVAL;
     }
-    // a row never fills its table past half: 2^log2_slots >= 2 * degree
-    if (((int64_t)1 << s.log2_slots) < 2 * s.max_degree) return LEIDEN_EINVAL;
+    // a row never fills its table past half: 2^log2_slots >= 2 * degree; a
+    // one-lane tier holds the whole row in 2^log2_slots registers
+    if (s.kind == LEIDEN_TIER_GROUP && s.lanes == 1) {
+      if (((int64_t)1 << s.log2_slots) < s.max_degree) return LEIDEN_EINVAL;
+    } else if (((int64_t)1 << s.log2_slots) < 2 * s.max_degree) {
+      return LEIDEN_EINVAL;
+    }
   }
   return LEIDEN_OK;
 }
@@ -133,6 +139,9 @@ std::vector<leiden_tier_table> candidates() {
   leiden_tier_table d{};
   leiden_tiers_default(&d);
   v.push_back(d);
+  // warp groups of 4 and 8 lanes with shared tables for the shortest rows
+  v.push_back(make({G(4, 3, 256, 4), G(8, 4, 256, 8), G(16, 5, 256, 16), G(32, 6, 256, 32), G(32, 8, 256, 128),
+                    G(32, 9, 256, 256), B(10, 128, 512), B(12, 256, 2048), B(14, 512, 8192), HUB()}));
   // sparser tables for short rows (fewer probe collisions)
   v.push_back(make({G(4, 4, 256, 4), G(8, 5, 256, 8), G(16, 6, 256, 16), G(32, 7, 256, 32), G(32, 9, 256, 128),
                     G(32, 10, 128, 512), B(12, 256, 2048), B(14, 512, 8192), HUB()}));

@@ -260,6 +260,41 @@ def test_apply_batch_matches_oracle(ctx, frac):
     assert np.array_equal(gt.w.cpu().numpy().astype(np.int64), ref[2])
 
 
+def test_apply_batch_edge_cases(ctx):
+    off, idx, w = GRAPHS["pp_strong"]()
+    n = len(off) - 1
+    G = L.Graph.from_numpy(off, idx, w)
+    eu, ev, ew = S.undirected_pairs(off, idx, w)
+    E = L.Edges.from_numpy
+    cases = [
+        (None, None),                                                        # copy only
+        ((eu[:3].astype(np.int32), ev[:3].astype(np.int32), ew[:3].astype(np.int32)),
+         (eu[:3].astype(np.int32), ev[:3].astype(np.int32), np.full(3, 5, np.int32))),  # delete, then reinsert
+        (None, (np.zeros(40, np.int32), np.arange(1, 41, dtype=np.int32), np.ones(40, np.int32))),  # one long row
+        ((eu[-2:].astype(np.int32), ev[-2:].astype(np.int32), ew[-2:].astype(np.int32)), None),  # deletions only
+    ]
+    for dels, ins in cases:
+        ref = O.apply_batch(off, idx, w, dels, ins)
+        gt = ctx.apply_batch(G, E(dels) if dels else None, E(ins) if ins else None)
+        assert np.array_equal(gt.off.cpu().numpy(), ref[0])
+        assert np.array_equal(gt.idx.cpu().numpy(), ref[1])
+        assert np.array_equal(gt.w.cpu().numpy().astype(np.int64), ref[2])
+    # a graph of isolated vertices gets its first edges
+    iso = (np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))
+    ins = (np.arange(0, 20, dtype=np.int32), np.arange(20, 40, dtype=np.int32), np.full(20, 2, np.int32))
+    ref = O.apply_batch(*iso, None, ins)
+    gt = ctx.apply_batch(L.Graph.from_numpy(*iso), None, E(ins))
+    assert np.array_equal(gt.off.cpu().numpy(), ref[0]) and np.array_equal(gt.idx.cpu().numpy(), ref[1])
+    # an unsorted row is refused, whether or not the batch touches it
+    bad = idx.copy()
+    r = int(np.argmax(np.diff(off) >= 3))
+    bad[off[r]], bad[off[r] + 1] = bad[off[r] + 1], bad[off[r]]
+    for ins in (None, (np.array([r], np.int32), np.array([(r + 1) % n], np.int32), np.ones(1, np.int32))):
+        with pytest.raises(L.LeidenError) as ei:
+            ctx.apply_batch(L.Graph.from_numpy(off, bad, w), None, E(ins) if ins else None)
+        assert ei.value.code == -1
+
+
 def test_apply_batch_rejects_bad_batches(ctx):
     off, idx, w = S.ring_of_cliques(3, 3)
     G = L.Graph.from_numpy(off, idx, w)
