@@ -72,6 +72,10 @@ def parse():
                     help="skip the compact R-MAT scale-22 figures of the default Chung-Lu line")
     ap.add_argument("--cl-div", type=int, default=1,
                     help="--profile-static on the Chung-Lu recipe at 1/k of its vertices and edges")
+    ap.add_argument("--record-traffic", default=None,
+                    help="ncu CSV of the first-pass decide kernels' DRAM bytes: write the traffic figure of the "
+                         "workload to profiles/ (with --profile-json, the JSON line of the profiled run)")
+    ap.add_argument("--profile-json", default=None)
     ap.add_argument("--profile-static", action="store_true",
                     help="run one Static Leiden on the workload graph and print its statistics (for profilers)")
     ap.add_argument("--lowdeg-samples", type=int, default=3, help="batches per size on the low-degree graphs")
@@ -1221,6 +1225,55 @@ def run_smscale(args):
     return 0
 
 
+DECIDE_KERNEL_PREFIXES = ("decide_", "hub_")
+
+
+def record_traffic(args):
+    """Writes profiles/decide_traffic_<workload>.json from an ncu capture of
+    the first pass's local-moving range (--metrics dram__bytes_read.sum,
+    dram__bytes_write.sum, gpu__time_duration.sum; --nvtx-include
+    "local_move_pass0/") and the JSON line the same --profile-static command
+    printed: DRAM bytes of the decide kernels per colour class and per scanned
+    CSR entry, next to their algorithmic bytes."""
+    import csv
+    rows = list(csv.reader(open(args.record_traffic)))
+    start = next(k for k, r in enumerate(rows) if r and r[0] == "ID")
+    hdr = rows[start]
+    ki, mn, mv, mu = (hdr.index(x) for x in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit"))
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-9, "usecond": 1e-6,
+             "msecond": 1e-3, "second": 1.0}
+    rd = wr = 0.0
+    kernels = 0
+    for r in rows[start + 1:]:
+        if len(r) <= mv or not r[ki].split("<")[0].split("(")[0].replace("void ", "").strip().startswith(
+                DECIDE_KERNEL_PREFIXES):
+            continue
+        v = float(r[mv].replace(",", "")) * scale.get(r[mu], 1.0)
+        if r[mn] == "dram__bytes_read.sum":
+            rd += v
+            kernels += 1
+        elif r[mn] == "dram__bytes_write.sum":
+            wr += v
+    prof = None
+    for ln in open(args.profile_json):
+        ln = ln.strip()
+        if ln.startswith("{"):
+            prof = json.loads(ln)
+    subs = prof["move0_kernel_launches"]
+    out = {"workload": prof["workload"], "capture": os.path.basename(args.record_traffic),
+           "source_sha256": decide_sources_sha(), "sub_sweeps": subs, "decide_kernel_launches": kernels,
+           "dram_read_bytes": rd, "dram_write_bytes": wr,
+           "dram_bytes_per_launch": (rd + wr) / subs,
+           "algorithmic_bytes_per_launch": prof["move0_bytes"] / subs,
+           "scanned_entries_per_launch": prof["move0_scanned_entries"] / subs,
+           "dram_bytes_per_scanned_entry": (rd + wr) / prof["move0_scanned_entries"]}
+    path = TRAFFIC_FILES[args.workload]
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
+    return 0
+
+
 def run_profile_static(args):
     """One Static Leiden (DET) on the workload's graph (``--workload cl`` or
     ``rmat``; ``--cl-div k`` takes the Chung-Lu recipe at 1/k of the vertices
@@ -1261,6 +1314,8 @@ def run_profile_static(args):
 
 def main():
     args = parse()
+    if args.record_traffic:
+        return record_traffic(args)
     if args.profile_static:
         return run_profile_static(args)
     if args.impl == "reference":

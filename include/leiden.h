@@ -255,9 +255,8 @@ int leiden_modularity_noalloc(const leiden_csr *g, const int32_t *membership, do
  * leiden_static / leiden_update: for each graph the membership, modularity
  * and per-pass statistics are bit-identical to those calls.  Meant for graphs
  * small enough that one thread block per graph keeps the GPU busy; larger
- * graphs belong to a leiden_ctx.  ND and DF updates recompute K^t and
- * Sigma^t from G^t and C^{t-1} (Alg. update with no auxiliary input); DS is
- * not offered here.
+ * graphs belong to a leiden_ctx.  ND, DS and DF updates recompute K^t and
+ * Sigma^t from G^t and C^{t-1} (Alg. update with no auxiliary input).
  * ------------------------------------------------------------------------- */
 typedef struct leiden_batch leiden_batch;
 
@@ -278,10 +277,10 @@ enum { LEIDEN_STATIC = 0 };  /* leiden_batch_item.mode for Static Leiden */
 
 typedef struct {
   leiden_csr g;              /* the graph (G^t for updates); DEVICE pointers */
-  int32_t mode;              /* LEIDEN_STATIC, LEIDEN_ND or LEIDEN_DF */
+  int32_t mode;              /* LEIDEN_STATIC, LEIDEN_ND, LEIDEN_DS or LEIDEN_DF */
   int32_t reserved;          /* must be 0 */
-  const int32_t *prior;      /* DEVICE [n]: C^{t-1}, labels in [0, n) (ND / DF) */
-  leiden_edges del, ins;     /* DEVICE: the batch that turned G^{t-1} into G^t (ND / DF) */
+  const int32_t *prior;      /* DEVICE [n]: C^{t-1}, labels in [0, n) (ND / DS / DF) */
+  leiden_edges del, ins;     /* DEVICE: the batch that turned G^{t-1} into G^t (ND / DS / DF) */
   int32_t *membership_out;   /* DEVICE [n]: canonical labels */
 } leiden_batch_item;
 
@@ -347,7 +346,7 @@ typedef struct {
   int64_t small_batch_n;     /* vertices / entries summed over one persistent launch */
   int64_t small_batch_nnz;
   double growth;             /* spare CSR capacity of a resident graph, as a fraction of its nnz */
-  int32_t mode;              /* LEIDEN_DF (default when 0) or LEIDEN_ND */
+  int32_t mode;              /* LEIDEN_DF (default when 0), LEIDEN_DS or LEIDEN_ND */
   int32_t autotune_trials;   /* > 0: leiden_autotune each large graph at admission with this many
                               * candidate tier tables and use its table for the graph's runs */
   int32_t small_workers;     /* workers for small graphs, each with its own persistent launch in

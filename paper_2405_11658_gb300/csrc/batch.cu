@@ -78,7 +78,7 @@ int check_item(const leiden_batch_item &it) {
   if (g.n > 0 && !it.membership_out) return LEIDEN_EINVAL;
   if (it.reserved != 0) return LEIDEN_EINVAL;
   if (it.mode == LEIDEN_STATIC) return LEIDEN_OK;
-  if (it.mode != LEIDEN_ND && it.mode != LEIDEN_DF) return LEIDEN_EINVAL;
+  if (it.mode != LEIDEN_ND && it.mode != LEIDEN_DS && it.mode != LEIDEN_DF) return LEIDEN_EINVAL;
   if (g.n > 0 && !it.prior) return LEIDEN_EINVAL;
   if (it.del.count < 0 || it.ins.count < 0) return LEIDEN_EINVAL;
   if (it.del.count > 0 && (!it.del.src || !it.del.dst || !it.del.w)) return LEIDEN_EINVAL;

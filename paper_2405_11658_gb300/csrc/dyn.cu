@@ -276,22 +276,25 @@ __global__ void ba_copy_k(int64_t nnz, int64_t T, const int32_t *trow, const int
     }
   }
 }
-// One warp per touched row: every surviving old entry goes to its rank among
-// the new row (its position less the removed entries before it plus the new
-// ones before it), every new entry likewise.
+// BA_MERGE_LANES lanes per touched row (most touched rows are short, so a
+// whole warp per row would leave most lanes idle): every surviving old entry
+// goes to its rank among the new row (its position less the removed entries
+// before it plus the new ones before it), every new entry likewise.
+static constexpr int BA_MERGE_LANES = 8;
 __global__ void ba_merge_k(int64_t T, const int32_t *trow, const int64_t *uoff, const int64_t *nrec,
                            const int32_t *ut, const int32_t *uw, const uint8_t *uk, const int32_t *Rp,
                            const int32_t *Np, const int64_t *off, const int32_t *idx, const int32_t *w,
                            const int64_t *off2, int32_t *idx2, int32_t *w2, u64 *err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  constexpr int G = BA_MERGE_LANES;
+  const int lane = threadIdx.x % G;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / G;
   for (int64_t t = wid; t < T; t += nwarps) {
     const int32_t u = trow[t];
     const int64_t a0 = off[u], a1 = off[u + 1];
     const int64_t p0 = uoff[u], nr = nrec[u];
     const int64_t o0 = off2[u], len = off2[u + 1] - o0;
-    for (int64_t a = a0 + lane; a < a1; a += 32) {
+    for (int64_t a = a0 + lane; a < a1; a += G) {
       const int32_t x = idx[a];
       if (a > a0 && idx[a - 1] >= x) { atomicOr(err, 8ull); continue; }
       int64_t lo = 0, hi = nr;                                 // first record with target >= x
@@ -316,7 +319,7 @@ __global__ void ba_merge_k(int64_t T, const int32_t *trow, const int64_t *uoff, 
       idx2[o0 + pos] = x;
       w2[o0 + pos] = wt;
     }
-    for (int64_t q = lane; q < nr; q += 32) {
+    for (int64_t q = lane; q < nr; q += G) {
       if (uk[p0 + q] != UPD_NEW) continue;
       const int32_t y = ut[p0 + q];
       const int64_t pos = (row_find(idx, a0, a1, y) - a0) - Rp[p0 + q] + Np[p0 + q];
@@ -377,7 +380,7 @@ int apply_batch(int64_t n, const int64_t *off, const int32_t *idx, const int32_t
                                                                          wk.bits, nnz2, idx_out, w_out, wk.err);
   }
   if (T > 0)
-    LK_COUNTED ba_merge_k<<<gridd(T * 32, 256, 152 * 32), 256, 0, s>>>(T, wk.trow, wk.uoff, wk.cnt, wk.ut, wk.uw,
+    LK_COUNTED ba_merge_k<<<gridd(T * BA_MERGE_LANES, 256, 152 * 32), 256, 0, s>>>(T, wk.trow, wk.uoff, wk.cnt, wk.ut, wk.uw,
                                                                       wk.uk, wk.Rp, wk.Np, off, idx, w, off_out,
                                                                       idx_out, w_out, wk.err);
   cudaMemcpyAsync(&herr, wk.err, sizeof(u64), cudaMemcpyDeviceToHost, s);

@@ -17,6 +17,10 @@
 // Work counts stay on the device: grids are fixed and stride over them.
 #include <limits.h>
 
+#include <algorithm>
+
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -39,7 +43,7 @@ __device__ __forceinline__ bool hub_eligible(const MoveArgs<WT> &a, int32_t i, b
 // (0 when not eligible), insert-work offset ioff[k] and scan-work offset
 // soff[k]; the totals go to hw.tot[0..2].
 template <typename WT>
-__global__ void __launch_bounds__(1024) hub_prep_k(MoveArgs<WT> a, bool refine, HubWork hw) {
+__global__ void __launch_bounds__(1024) hub_prep_k(MoveArgs<WT> a, bool refine, HubWork hw, int64_t cluster_cap) {
   __shared__ int64_t warp_s[3][32];
   __shared__ int64_t carry[3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -50,17 +54,23 @@ __global__ void __launch_bounds__(1024) hub_prep_k(MoveArgs<WT> a, bool refine, 
     int64_t v[3] = {0, 0, 0};
     if (k < a.list_n) {
       const int32_t i = a.list[k];
+      int64_t tsz = 0;
       if (hub_eligible(a, i, refine)) {
         const int64_t deg = a.g.off[i + 1] - a.g.off[i];
         const int64_t cap = deg < a.g.n ? deg : a.g.n;
-        // at least twice the distinct keys, in whole scan chunks (the home
-        // slot comes from a multiply-shift, so any size works)
-        const int64_t t = ((2 * cap + HUB_SCAN_CHUNK - 1) / HUB_SCAN_CHUNK) * HUB_SCAN_CHUNK;
-        v[0] = t;
-        v[1] = (deg + HUB_CHUNK - 1) / HUB_CHUNK;
-        v[2] = t / HUB_SCAN_CHUNK;
+        if (cap <= cluster_cap) {
+          tsz = -1;  // decided by a cluster with the table in distributed shared memory
+        } else {
+          // at least twice the distinct keys, in whole scan chunks (the home
+          // slot comes from a multiply-shift, so any size works)
+          const int64_t t = ((2 * cap + HUB_SCAN_CHUNK - 1) / HUB_SCAN_CHUNK) * HUB_SCAN_CHUNK;
+          v[0] = t;
+          v[1] = (deg + HUB_CHUNK - 1) / HUB_CHUNK;
+          v[2] = t / HUB_SCAN_CHUNK;
+          tsz = t;
+        }
       }
-      hw.tsz[k] = v[0];
+      hw.tsz[k] = tsz;
     }
     // block-wide exclusive scans of the three counts
     int64_t incl[3];
@@ -220,7 +230,7 @@ template <typename WT, typename ST, bool REFINE, bool ASYNC>
 __global__ void __launch_bounds__(256) hub_final_k(MoveArgs<WT> a, HubWork hw) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.list_n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    if (hw.tsz[k] == 0) continue;  // not eligible
+    if (hw.tsz[k] <= 0) continue;  // not eligible, or decided by a cluster
     const int32_t i = a.list[k];
     const int32_t d = a.C[i];
     i128 bsc = 0;
@@ -277,6 +287,216 @@ __global__ void __launch_bounds__(256) hub_final_k(MoveArgs<WT> a, HubWork hw) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster path: one thread-block cluster of HC_CTAS CTAs decides one hub at a
+// time, its hashtable spread over the CTAs' shared memory (distributed shared
+// memory, HC_SLOTS slots per CTA; slot s lives in CTA s / HC_SLOTS).  The
+// CTAs split the row, combine equal communities per warp and insert into the
+// owning CTA's slice with shared-memory atomics across the cluster; after a
+// cluster barrier each CTA scans its own slice, and CTA 0 reduces the slices'
+// bests and takes the decision (Eq. 2 scaled, the move rule) -- one kernel
+// instead of the insert / scan / final chain through global memory, for hubs
+// with at most HC_CTAS * HC_SLOTS / 2 distinct candidates.
+// ---------------------------------------------------------------------------
+static constexpr int HC_CTAS = 8;
+static constexpr int HC_LOG2 = 14;
+static constexpr uint32_t HC_SLOTS = 1u << HC_LOG2;
+static constexpr int HC_THREADS = 512;
+
+template <typename WT, typename ST, bool REFINE, bool ASYNC>
+__global__ void __launch_bounds__(HC_THREADS) hub_cluster_k(MoveArgs<WT> a, HubWork hw) {
+  namespace cg = cooperative_groups;
+  typedef typename TableVal<ST>::type VT;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  VT *vals = reinterpret_cast<VT *>(smem);
+  int32_t *keys = reinterpret_cast<int32_t *>(vals + HC_SLOTS);
+  __shared__ u64 wscratch[HC_THREADS / 32][32];
+  __shared__ ST r_sc[HC_THREADS / 32];
+  __shared__ int32_t r_c[HC_THREADS / 32];
+  __shared__ int64_t r_kid[HC_THREADS / 32];
+  __shared__ int64_t r_cand[HC_THREADS / 32];
+  __shared__ ST p_sc;        // this CTA's best over its slice, read by CTA 0
+  __shared__ int32_t p_c;
+  __shared__ int64_t p_kid;
+  const unsigned rank = cl.block_rank();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t cid = blockIdx.x / HC_CTAS, ncl = gridDim.x / HC_CTAS;
+  for (int64_t k = cid; k < a.list_n; k += ncl) {   // the same k in every CTA of the cluster
+    if (hw.tsz[k] >= 0) continue;                    // not eligible, or on the global path
+    const int32_t i = a.list[k];
+    const int64_t e0 = a.g.off[i], e1 = a.g.off[i + 1];
+    // the hub's table: at least twice its distinct candidates, a power of two
+    // of slots per CTA (at most HC_SLOTS); clearing and scanning cost its size
+    const int64_t cap = (e1 - e0) < a.g.n ? (e1 - e0) : a.g.n;
+    int lg = 8;
+    while (lg < HC_LOG2 && ((int64_t)HC_CTAS << lg) < 2 * cap) lg++;
+    const uint32_t LS = 1u << lg;                    // slots per CTA for this hub
+    const uint64_t TT = (uint64_t)LS * HC_CTAS;
+    for (uint32_t sl = threadIdx.x; sl < LS; sl += blockDim.x) { keys[sl] = LEIDEN_EMPTY_KEY; vals[sl] = 0; }
+    cl.sync();
+    const int32_t cbi = REFINE ? a.CB[i] : 0;
+    const int64_t stride = (int64_t)HC_CTAS * blockDim.x;
+    for (int64_t base = e0 + (int64_t)rank * blockDim.x + warp * 32; base < e1; base += stride) {
+      const int64_t e = base + lane;
+      int32_t c = LEIDEN_EMPTY_KEY;
+      u64 wv = 0;
+      if (e < e1) {
+        const int32_t j = a.g.idx[e];
+        bool ok = j != i;
+        if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
+        if (REFINE && ok && a.CB[j] != cbi) ok = false;
+        if (ok) { c = a.C[j]; wv = (u64)(int64_t)a.g.w[e]; }
+      }
+      u64 sum = 0;
+      if (warp_combine((unsigned long long)(uint32_t)c, c != LEIDEN_EMPTY_KEY, wv, &sum, wscratch[warp])) {
+        uint64_t sl = ((uint64_t)hash32(c) * TT) >> 32;
+        bool done = false;
+        for (uint64_t probe = 0; probe < TT && !done; probe++) {
+          const unsigned owner = (unsigned)(sl >> lg);
+          const uint32_t loc = (uint32_t)(sl & (LS - 1));
+          int32_t *kp = cl.map_shared_rank(keys, owner) + loc;
+          VT *vp = cl.map_shared_rank(vals, owner) + loc;
+          const int32_t kk = *(volatile int32_t *)kp;
+          if (kk == c) { add_val(vp, sum); done = true; break; }
+          if (kk == LEIDEN_EMPTY_KEY) {
+            const int32_t old = atomicCAS(kp, LEIDEN_EMPTY_KEY, c);
+            if (old == LEIDEN_EMPTY_KEY || old == c) { add_val(vp, sum); done = true; break; }
+          }
+          sl = sl + 1 == TT ? 0 : sl + 1;
+        }
+        if (!done) atomicOr(&a.ctr[CTR_ERROR], 16ull);
+      }
+    }
+    cl.sync();
+    // this CTA's slice: best candidate and the weight towards the own community
+    const int32_t d = a.C[i];
+    const int64_t Ki = a.K[i];
+    const ST A = (ST)a.A, B = (ST)a.p * (ST)Ki;
+    ST bsc = 0;
+    int32_t bc = INT32_MAX;
+    int64_t kid = 0, cand = 0;
+    for (uint32_t sl = threadIdx.x; sl < LS; sl += blockDim.x) {
+      const int32_t c = keys[sl];
+      if (c == LEIDEN_EMPTY_KEY) continue;
+      const int64_t v = (int64_t)vals[sl];
+      cand++;
+      if (c == d) { kid = v; continue; }
+      const ST sc = A * (ST)v - B * (ST)a.Sig[c];
+      if (hub_better<WT, ST>(sc, c, bsc, bc)) { bsc = sc; bc = c; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const ST osc = shfl_xor_any<ST>(bsc, o);
+      const int32_t oc = __shfl_xor_sync(FULL_MASK, bc, o);
+      kid += shfl_xor_i64(kid, o);
+      cand += shfl_xor_i64(cand, o);
+      if (hub_better<WT, ST>(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
+    }
+    if (lane == 0) { r_sc[warp] = bsc; r_c[warp] = bc; r_kid[warp] = kid; r_cand[warp] = cand; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < (int)(blockDim.x >> 5); q++) {
+        kid += r_kid[q];
+        cand += r_cand[q];
+        if (hub_better<WT, ST>(r_sc[q], r_c[q], bsc, bc)) { bsc = r_sc[q]; bc = r_c[q]; }
+      }
+      p_sc = bsc;
+      p_c = bc;
+      p_kid = kid;
+      if (cand) atomicAdd(&a.ctr[CTR_CANDIDATES], (u64)cand);
+    }
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+      for (unsigned r = 1; r < HC_CTAS; r++) {
+        const ST osc = *cl.map_shared_rank(&p_sc, r);
+        const int32_t oc = *cl.map_shared_rank(&p_c, r);
+        kid += *cl.map_shared_rank(&p_kid, r);
+        if (hub_better<WT, ST>(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
+      }
+      atomicAdd(&a.ctr[CTR_SCANNED_ENTRIES], (u64)(e1 - e0));
+      atomicAdd(&a.ctr[CTR_SCANNED_VERTICES], 1ull);
+      bool go = bc != INT32_MAX;
+      i128 S = 0;
+      if (go) {
+        S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - a.Sig[d]);
+        go = S > 0;
+        if (REFINE && go && a.C[bc] != bc) go = false;
+      }
+      if (go && ASYNC) {
+        bool ok;
+        if (!REFINE) {
+          ok = !(a.Sig[d] == Ki && a.Sig[bc] == a.K[bc] && bc > d);  // minimum-label rule
+          if (ok) {
+            atomic_add_i64(&a.Sig[d], -Ki);
+            atomic_add_i64(&a.Sig[bc], Ki);
+            a.C[i] = bc;
+            if (a.dynamic) { a.changed[d] = 1; a.changed[bc] = 1; }
+            const u64 slot = atomicAdd(&a.ctr[CTR_BIG], 1ull);  // neighbours re-marked by the big-row kernel
+            a.big[slot] = i;
+          }
+        } else {
+          ok = false;
+          const u64 old = atomicCAS((u64 *)&a.Sig[i], (u64)Ki, 0ull);
+          if ((int64_t)old == Ki) {
+            const u64 prev = atomicAdd((u64 *)&a.Sig[bc], (u64)Ki);
+            if (prev == 0ull) {
+              atomic_add_i64(&a.Sig[bc], -Ki);
+              atomic_add_i64(&a.Sig[i], Ki);
+            } else {
+              a.C[i] = bc;
+              ok = true;
+            }
+          }
+        }
+        if (ok) {
+          atomicAdd(&a.ctr[CTR_MOVES], 1ull);
+          atomic_add_i128(&a.ctr[CTR_SUMS_LO], S);
+        }
+      } else if (go) {
+        const u64 slot = atomicAdd(a.prop_count, 1ull);
+        a.prop_i[slot] = i;
+        a.prop_c[slot] = bc;
+        a.prop_S[slot] = S;
+        if (REFINE) a.stamp[i] = a.stamp_val;
+      }
+    }
+    cl.sync();   // CTA 0 has read every slice's best before the next hub reuses them
+  }
+}
+
+// Clusters resident at once for the cluster path (0: not available), per
+// instantiation, queried once.
+template <typename WT, typename ST, bool REFINE, bool ASYNC>
+static int hub_clusters() {
+  static int n = -1;
+  if (n >= 0) return n;
+  auto k = hub_cluster_k<WT, ST, REFINE, ASYNC>;
+  const size_t smem = (size_t)HC_SLOTS * (sizeof(typename TableVal<ST>::type) + sizeof(int32_t));
+  n = 0;
+  if (cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return n;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(HC_CTAS, 1, 1);
+  cfg.blockDim = dim3(HC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr{};
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = HC_CTAS;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int c = 0;
+  if (cudaOccupancyMaxActiveClusters(&c, (const void *)k, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    c = 0;
+  }
+  n = c;
+  return n;
+}
+
 // Re-marks the neighbours of long movers as unprocessed: every block walks
 // every listed row, so one long row is spread over the whole grid.
 __global__ void __launch_bounds__(256) mark_big_rows_k(const int32_t *big, const u64 *count, const int64_t *off,
@@ -311,7 +531,26 @@ void launch_mark_big(const int32_t *big, const u64 *count, const int64_t *off, c
 template <typename WT, typename ST, bool REFINE, bool ASYNC>
 void launch_hubs(const MoveArgs<WT> &a, const HubWork &hw, int sms, cudaStream_t s) {
   if (a.list_n <= 0) return;
-  LK_COUNTED hub_prep_k<WT><<<1, 1024, 0, s>>>(a, REFINE, hw);
+  const int ncl = LK_HUB_CLUSTERS ? hub_clusters<WT, ST, REFINE, ASYNC>() : 0;
+  const int64_t cluster_cap = ncl > 0 ? (int64_t)HC_CTAS * HC_SLOTS / 2 : 0;
+  LK_COUNTED hub_prep_k<WT><<<1, 1024, 0, s>>>(a, REFINE, hw, cluster_cap);
+  if (ncl > 0) {
+    int64_t nc = std::min<int64_t>(ncl, a.list_n);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(nc * HC_CTAS), 1, 1);
+    cfg.blockDim = dim3(HC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)HC_SLOTS * (sizeof(typename TableVal<ST>::type) + sizeof(int32_t));
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = HC_CTAS;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    note_launch();
+    cudaLaunchKernelEx(&cfg, hub_cluster_k<WT, ST, REFINE, ASYNC>, a, hw);
+  }
   LK_COUNTED hub_insert_k<WT, typename TableVal<ST>::type><<<sms * 8, 256, 0, s>>>(a, REFINE, hw);
   LK_COUNTED hub_scan_k<WT, ST><<<sms * 8, 256, 0, s>>>(a, hw);
   LK_COUNTED hub_final_k<WT, ST, REFINE, ASYNC><<<(unsigned)((a.list_n + 255) / 256), 256, 0, s>>>(a, hw);

@@ -127,11 +127,25 @@ static constexpr int64_t HUB_TABLE_MIN = 4096;
 // 6 Mi keeps a round's tables resident in L2.  LK_AUX_STREAMS is the number of
 // auxiliary streams the tier kernels of a sub-sweep fan out to (0: all on the
 // context stream).
+// 1: aggregation gives communities of 385..1024 entries their own block tier
+// (128 threads, 2048 slots) instead of the 256-thread, 4096-slot one.
+#ifndef LK_AGG_SPLIT
+#define LK_AGG_SPLIT 1
+#endif
 #ifndef LK_AGG_ROUND_SLOTS
 #define LK_AGG_ROUND_SLOTS 0
 #endif
 #ifndef LK_HUB_ROUND_SLOTS
 #define LK_HUB_ROUND_SLOTS 0
+#endif
+// 1: hub rows with at most 64 Ki distinct candidates are decided by a thread-
+// block cluster with the table in distributed shared memory (0: every hub row
+// through the global-memory tables).  Same decisions either way; measured
+// slower on Chung-Lu (3.33 against 2.92 s per Static) and R-MAT scale 22 (170
+// against 149 ms): a cluster holds eight SMs per hub and the other degree
+// tiers of the colour class wait for them.
+#ifndef LK_HUB_CLUSTERS
+#define LK_HUB_CLUSTERS 0
 #endif
 // 1: every level compares candidate scores in 128 bits, whatever its
 // largest K' (a testing aid: both widths must give the same decisions).

@@ -415,7 +415,7 @@ extern "C" int leiden_server_create(leiden_server **out, const leiden_server_con
   if (!out || !cfg) return LEIDEN_EINVAL;
   leiden_server_config c = *cfg;
   if (c.mode == 0) c.mode = LEIDEN_DF;
-  if (c.mode != LEIDEN_DF && c.mode != LEIDEN_ND) return LEIDEN_EINVAL;
+  if (c.mode != LEIDEN_DF && c.mode != LEIDEN_ND && c.mode != LEIDEN_DS) return LEIDEN_EINVAL;
   if (c.small_workers == 0) c.small_workers = 2;
   if (c.min_persistent == 0) c.min_persistent = 8;
   if (c.small_workers < 1 || c.small_workers > 8 || c.min_persistent < 1) return LEIDEN_EINVAL;

@@ -88,7 +88,8 @@ struct Ctl {
   int64_t p, q, two_m;
   double den;      // (2m)^2 / 2 * q
   int log2S;
-  int dynamic;     // changed flags follow the moves (first pass of ND / DF)
+  int dynamic;     // changed flags follow the moves (first pass of ND / DS / DF)
+  const uint8_t *in_range;  // DS affected range in the first pass, else NULL
 };
 
 __device__ __forceinline__ bool better128(i128 sc, int32_t c, i128 bsc, int32_t bc) {
@@ -246,6 +247,7 @@ __device__ void decide(const Lvl<WT> &g, WS &w, const Ctl &ct, int32_t kb, int32
         if (!REFINE) {
           act = !w.proc[i];
           w.proc[i] = 1;
+          if (act && ct.in_range) act = ct.in_range[i] != 0;   // inAffectedRange (Alg. delta)
         } else {
           act = w.ch[w.CB[i]] && w.Cp[i] == i && w.Sp[i] == w.Kp[i];
         }
@@ -758,6 +760,73 @@ __device__ int check_job(const SmallJob &j, Shared &sm) {
   return rc;
 }
 
+// Alg. delta inside one block: the affected vertices (w.flag, the range of
+// the first pass; they start unprocessed), with w.ch2 as delta-E (vertices
+// whose neighbours are affected) and w.stamp as delta-C (communities whose
+// members are affected).  Deletions inside a community mark both ends and the
+// community; for each source of insertions, the best community c* != its own
+// by Eq. 2 with K_{i->c} the inserted weight towards c and K_{i->d} = 0 (ties
+// to the smallest c) marks the source and c*.  K and Sigma are those of G^t
+// and C^{t-1} (w.Kp, w.Sp).  Batches of the persistent path are small: each
+// source's insertions are grouped by scanning the batch.
+__device__ void mark_ds(const SmallJob &j, WS &w, const Ctl &ct, Shared &sm) {
+  const int64_t N = j.n;
+  uint8_t *aff = w.flag, *dE = w.ch2, *dC = w.stamp;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) { aff[i] = 0; dE[i] = 0; dC[i] = 0; }
+  __syncthreads();
+  for (int64_t k = threadIdx.x; k < j.nd; k += blockDim.x) {
+    const int32_t u = j.ds[k], v = j.dd[k];
+    const int32_t c = j.prior[u];
+    if (c != j.prior[v]) continue;
+    aff[u] = 1; dE[u] = 1;
+    aff[v] = 1; dE[v] = 1;
+    dC[c] = 1;
+  }
+  // directed insertion entries x in [0, 2 ni): (is, id) then (id, is)
+  const int64_t E = 2 * j.ni;
+  auto src = [&](int64_t x) { return x < j.ni ? j.is[x] : j.id[x - j.ni]; };
+  auto dst = [&](int64_t x) { return x < j.ni ? j.id[x] : j.is[x - j.ni]; };
+  auto wt = [&](int64_t x) { return (int64_t)(x < j.ni ? j.iw[x] : j.iw[x - j.ni]); };
+  for (int64_t x = threadIdx.x; x < E; x += blockDim.x) {
+    const int32_t u = src(x);
+    bool first = true;
+    for (int64_t y = 0; y < x && first; y++) first = src(y) != u;
+    if (!first) continue;
+    const int32_t d = j.prior[u];
+    const int64_t Ki = w.Kp[u];
+    int32_t best = INT32_MAX;
+    i128 bS = 0;
+    for (int64_t y = x; y < E; y++) {
+      if (src(y) != u) continue;
+      const int32_t c = j.prior[dst(y)];
+      if (c == d) continue;
+      bool seen = false;
+      for (int64_t z = x; z < y && !seen; z++) seen = src(z) == u && j.prior[dst(z)] == c;
+      if (seen) continue;
+      int64_t h = 0;
+      for (int64_t z = y; z < E; z++)
+        if (src(z) == u && j.prior[dst(z)] == c) h += wt(z);
+      const i128 S = (i128)ct.A * h - (i128)ct.p * Ki * (Ki + w.Sp[c] - w.Sp[d]);
+      if (best == INT32_MAX || S > bS || (S == bS && c < best)) { bS = S; best = c; }
+    }
+    if (best != INT32_MAX) {
+      aff[u] = 1;
+      dE[u] = 1;
+      dC[best] = 1;
+    }
+  }
+  __syncthreads();
+  // expansion: members of delta-C communities and neighbours of delta-E vertices
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    if (dC[j.prior[i]]) aff[i] = 1;
+    if (dE[i])
+      for (int64_t e = j.off[i]; e < j.off[i + 1]; e++) aff[j.idx[e]] = 1;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) w.proc[i] = aff[i] ? 0 : 1;
+  __syncthreads();
+}
+
 // The whole of Alg. leiden for one job.
 __device__ void run_job(const SmallJob &j, const SmallOpts &o, SmallResult *res, int32_t *skeys, u64 *svals,
                         Shared &sm) {
@@ -801,6 +870,7 @@ __device__ void run_job(const SmallJob &j, const SmallOpts &o, SmallResult *res,
   ct.log2S = o.log2S;
   const bool upd = j.mode != LEIDEN_STATIC;
   ct.dynamic = upd ? 1 : 0;
+  ct.in_range = nullptr;
   // initial state (Alg. leiden / update / naive / frontier)
   for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
     w.Ctop[i] = (int32_t)i;
@@ -822,6 +892,10 @@ __device__ void run_job(const SmallJob &j, const SmallOpts &o, SmallResult *res,
       if (j.mode == LEIDEN_DF && same == del) { w.proc[u] = 0; w.proc[v] = 0; }  // Alg. frontier
     }
     __syncthreads();
+    if (j.mode == LEIDEN_DS) {
+      mark_ds(j, w, ct, sm);
+      ct.in_range = w.flag;
+    }
     int64_t a = 0;
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) a += w.proc[i] == 0;
     a = bsum64(a, sm);
@@ -850,6 +924,7 @@ __device__ void run_job(const SmallJob &j, const SmallOpts &o, SmallResult *res,
       r = pass(gl, w, ct, lp, tau, o, N, off2, idx2, w2, &nc, &nnz2, res, skeys, svals, sm);
     }
     ct.dynamic = 0;
+    ct.in_range = nullptr;
     if (r == 1) break;
     cur = dst;
     nv = nc;

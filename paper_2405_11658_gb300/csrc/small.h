@@ -20,7 +20,7 @@ struct SmallJob {
   const int64_t *off;
   const int32_t *idx;
   const int32_t *w;
-  int32_t mode;      // LEIDEN_STATIC, LEIDEN_ND or LEIDEN_DF
+  int32_t mode;      // LEIDEN_STATIC, LEIDEN_ND, LEIDEN_DS or LEIDEN_DF
   int32_t pad0;
   const int32_t *prior;
   int64_t nd, ni;

@@ -62,3 +62,32 @@ def test_config_objects():
 def test_host_info_names_the_cores():
     h = bench.host_info()
     assert h["nproc"] == os.cpu_count()
+
+
+def test_record_traffic_reads_an_ncu_capture(monkeypatch, tmp_path):
+    hdr = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",' \
+          '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"'
+    rows = []
+    for k, (name, rd, wr) in enumerate([("void decide_group<16, 5, 0, 0, int, long>(MoveArgs<T5>)", 100.0, 10.0),
+                                        ("void hub_insert_k<int, unsigned int>(MoveArgs<T1>, bool, HubWork)", 2.0, 1.0),
+                                        ("apply_moves_k(const int *, long *)", 999.0, 999.0)]):
+        for metric, unit, v in (("dram__bytes_read.sum", "Mbyte", rd), ("dram__bytes_write.sum", "Mbyte", wr),
+                                ("gpu__time_duration.sum", "usecond", 5.0)):
+            rows.append(f'"{k}","1","python","h","{name}","1","13","(256, 1, 1)","(9, 1, 1)","0","10.3",'
+                        f'"Command line profiler metrics","{metric}","{unit}","{v}"')
+    csv_path = tmp_path / "cap.csv"
+    csv_path.write_text("==PROF== noise\n" + hdr + "\n" + "\n".join(rows) + "\n")
+    prof = tmp_path / "prof.log"
+    prof.write_text('log line\n{"workload": "w", "move0_kernel_launches": 2, "move0_bytes": 500e6, '
+                    '"move0_scanned_entries": 1000000}\n')
+    out = tmp_path / "traffic.json"
+    monkeypatch.setitem(bench.TRAFFIC_FILES, "cl", str(out))
+
+    class A:
+        record_traffic, profile_json, workload = str(csv_path), str(prof), "cl"
+    assert bench.record_traffic(A) == 0
+    d = json.loads(out.read_text())
+    assert d["dram_read_bytes"] == 102e6 and d["dram_write_bytes"] == 11e6   # apply kernel left out
+    assert d["dram_bytes_per_launch"] == 113e6 / 2 and d["algorithmic_bytes_per_launch"] == 250e6
+    assert d["dram_bytes_per_scanned_entry"] == 113.0
+    assert bench.measured_traffic("cl", 1000) == 113000.0

@@ -99,7 +99,7 @@ def make_update(name, frac, seed):
     return gt, prior.membership, K, sig, dels, ins
 
 
-@pytest.mark.parametrize("mode", ["ND", "DF"])
+@pytest.mark.parametrize("mode", ["ND", "DS", "DF"])
 def test_batch_updates_match_oracle(batch, mode):
     cases = [("pp_1e4", 1e-3, 1), ("rmat11", 1e-2, 2), ("grid", 1e-3, 3), ("chung_lu_w", 1e-2, 4),
              ("er_dense", 1e-3, 5), ("kmer", 1e-2, 6)]
