@@ -650,9 +650,6 @@ static TierTable agg_tiers(int uniform) {
   if (!uniform) {
     tt.t[k++] = {TIER_GROUP, 48, 32, 7, 256};     // warp, 128 slots
     tt.t[k++] = {TIER_GROUP, 384, 32, 10, 128};   // warp, 1024 slots
-#if LK_AGG_SPLIT
-    tt.t[k++] = {TIER_BLOCK, 1024, 0, 11, 128};   // block, 2048 slots (24 KB: 8 blocks per SM)
-#endif
     tt.t[k++] = {TIER_BLOCK, 2048, 0, 12, 256};   // block, 4096 slots (48 KB: 4 blocks per SM)
   }
   tt.t[k++] = {TIER_GLOBAL, INT64_MAX, 0, 0, 256};

@@ -127,11 +127,6 @@ static constexpr int64_t HUB_TABLE_MIN = 4096;
 // 6 Mi keeps a round's tables resident in L2.  LK_AUX_STREAMS is the number of
 // auxiliary streams the tier kernels of a sub-sweep fan out to (0: all on the
 // context stream).
-// 1: aggregation gives communities of 385..1024 entries their own block tier
-// (128 threads, 2048 slots) instead of the 256-thread, 4096-slot one.
-#ifndef LK_AGG_SPLIT
-#define LK_AGG_SPLIT 1
-#endif
 #ifndef LK_AGG_ROUND_SLOTS
 #define LK_AGG_ROUND_SLOTS 0
 #endif
@@ -216,6 +211,9 @@ int64_t bucket_blockhist_elems(int64_t n, int nkeys);
 
 // scan.cu
 void ensure_smem(const void *func, size_t bytes);
+// Blocks of `func` (threads, dynamic shared memory) resident at once on `sms`
+// SMs: the grid of a grid-stride kernel that leaves no partial last wave.
+int64_t resident_blocks(const void *func, int threads, size_t smem, int sms);
 template <typename TI>
 void exclusive_scan(const TI *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
 int64_t scan_tmp_elems(int64_t n);

@@ -494,16 +494,25 @@ __device__ __forceinline__ void list_new_slots(int slot, uint16_t *used, unsigne
   if (slot >= 0) used[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)slot;
 }
 
+// Block tier: one vertex at a time per block, its row spread over all warps.
+// Warp 0 stages the headers of the block's next 32 listed vertices at once
+// (eligibility, row bounds, C', K', Sigma'[d]) and keeps only the eligible
+// ones, so neither a skipped vertex nor a header load costs the block a
+// barrier or a round trip of its own.  A vertex takes two barriers: after the
+// row's inserts, and after the used-slot scan; warp 0 then combines the
+// warps' bests and proposes while the other warps start on the next row (the
+// used-slot counter alternates between two words for that reason).
 template <bool REFINE, bool ASYNC, typename WT, typename ST>
 __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int32_t s_i, s_d, s_act;
-  __shared__ int64_t s_e0, s_e1, s_K, s_Sd;
+  __shared__ int32_t h_i[32], h_d[32];
+  __shared__ int64_t h_e0[32], h_e1[32], h_K[32], h_Sd[32];
+  __shared__ int32_t s_nact[2];
   __shared__ ST r_sc[32];
   __shared__ int32_t r_c[32];
   __shared__ int64_t r_kid[32];
   __shared__ int32_t s_mv;
-  __shared__ unsigned s_nused;
+  __shared__ unsigned s_nused[2];
   typedef typename TableVal<ST>::type VT;
   const int Hmax = 1 << log2H;
   VT *vals = reinterpret_cast<VT *>(smem);
@@ -516,21 +525,26 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
   int64_t scanned = 0, nvert = 0, ncand = 0, nmoves = 0;
   i128 accS = 0;
   for (int s = threadIdx.x; s < Hmax; s += blockDim.x) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
-  if (threadIdx.x == 0) s_nused = 0;
-  for (int64_t li = blockIdx.x; li < a.list_n; li += gridDim.x) {
-    if (threadIdx.x == 0) {
-      // header loads as in the group tiers
-      const int32_t i = a.list[li];
+  if (threadIdx.x < 2) s_nused[threadIdx.x] = 0;
+  int par = 0;   // parity of the vertices this block has decided
+  int bpar = 0;  // parity of the staged batches
+  const int64_t stride = gridDim.x;
+  for (int64_t base = blockIdx.x; base < a.list_n; base += 32 * stride, bpar ^= 1) {
+    if (warp == 0) {
+      // header loads as in the group tiers, one listed vertex per lane
+      const int64_t li = base + (int64_t)lane * stride;
+      const bool valid = li < a.list_n;
+      const int32_t i = valid ? a.list[li] : 0;
       int64_t h0 = 0, h1 = 0, hK = 0, hSd = 0;
       int32_t hd = 0;
-      if (a.spec) {
+      if (a.spec && valid) {
         h0 = a.g.off[i];
         h1 = a.g.off[i + 1];
         hd = a.C[i];
         hK = a.K[i];
         if (!ASYNC) hSd = a.Sig[hd];
       }
-      const bool act = eligible<REFINE>(a, i);
+      const bool act = valid && eligible<REFINE>(a, i);
       if (!a.spec && act) {
         h0 = a.g.off[i];
         h1 = a.g.off[i + 1];
@@ -538,108 +552,130 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
         hK = a.K[i];
         if (!ASYNC) hSd = a.Sig[hd];
       }
-      s_i = i;
-      s_act = act;
-      if (act) { s_d = hd; s_e0 = h0; s_e1 = h1; s_K = hK; s_Sd = hSd; }
+      const unsigned m = __ballot_sync(FULL_MASK, act);
+      if (act) {
+        const int pos = __popc(m & ((1u << lane) - 1u));
+        h_i[pos] = i;
+        h_d[pos] = hd;
+        h_e0[pos] = h0;
+        h_e1[pos] = h1;
+        h_K[pos] = hK;
+        h_Sd[pos] = hSd;
+      }
+      if (lane == 0) s_nact[bpar] = __popc(m);
     }
     __syncthreads();
-    if (!s_act) { __syncthreads(); continue; }
-    const int32_t i = s_i, d = s_d;
-    const int64_t e0 = s_e0, e1 = s_e1;
-    // table sized for this row: at least 2 * degree slots, at most the tier's
-    int lh = 1;
-    while (lh < log2H && ((int64_t)1 << lh) < 2 * (e1 - e0)) lh++;
-    const int32_t cbi = REFINE ? a.CB[i] : 0;
-    // each warp walks 32-entry chunks (warp-uniform), combining equal
-    // communities across its lanes before the atomics
-    for (int64_t cb = e0 + 32 * warp; cb < e1; cb += 32 * (int64_t)nwarp * BLOCK_ROW_UNROLL) {
-      int32_t cc[BLOCK_ROW_UNROLL];
-      u64 wv[BLOCK_ROW_UNROLL];
+    const int nact = s_nact[bpar];
+    for (int k = 0; k < nact; k++, par ^= 1) {
+      const int32_t i = h_i[k], d = h_d[k];
+      const int64_t e0 = h_e0[k], e1 = h_e1[k];
+      // table sized for this row: at least 2 * degree slots, at most the tier's
+      int lh = 1;
+      while (lh < log2H && ((int64_t)1 << lh) < 2 * (e1 - e0)) lh++;
+      const int32_t cbi = REFINE ? a.CB[i] : 0;
+      // each warp walks 32-entry chunks (warp-uniform), combining equal
+      // communities across its lanes before the atomics
+      for (int64_t cb = e0 + 32 * warp; cb < e1; cb += 32 * (int64_t)nwarp * BLOCK_ROW_UNROLL) {
+        int32_t cc[BLOCK_ROW_UNROLL];
+        u64 wv[BLOCK_ROW_UNROLL];
 #pragma unroll
-      for (int u = 0; u < BLOCK_ROW_UNROLL; u++) {
-        const int64_t e = cb + (int64_t)u * 32 * nwarp + lane;
-        const bool in = e < e1;
-        const int32_t j = in ? a.g.idx[e] : -1;
-        wv[u] = in ? (u64)(int64_t)a.g.w[e] : 0;
-        bool ok = in && j != i;
-        if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
-        cc[u] = ok ? j : -1;
+        for (int u = 0; u < BLOCK_ROW_UNROLL; u++) {
+          const int64_t e = cb + (int64_t)u * 32 * nwarp + lane;
+          const bool in = e < e1;
+          const int32_t j = in ? a.g.idx[e] : -1;
+          wv[u] = in ? (u64)(int64_t)a.g.w[e] : 0;
+          bool ok = in && j != i;
+          if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
+          cc[u] = ok ? j : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < BLOCK_ROW_UNROLL; u++) {
+          const int32_t j = cc[u];
+          bool ok = j >= 0;
+          if (REFINE && ok && a.CB[j] != cbi) ok = false;
+          cc[u] = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
+        }
+#pragma unroll
+        for (int u = 0; u < BLOCK_ROW_UNROLL; u++) {
+          u64 sum = 0;
+          int slot = -1;
+          if (warp_combine((unsigned long long)(uint32_t)cc[u], cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum,
+                           wscratch[warp]))
+            slot = table_add_new(keys, vals, lh, cc[u], sum, &a.ctr[CTR_ERROR]);
+          list_new_slots(slot, used, &s_nused[par]);
+        }
+      }
+      if (threadIdx.x == 0) { scanned += e1 - e0; nvert++; }
+      __syncthreads();
+      const unsigned nused = s_nused[par];
+      const ST A = (ST)a.A;
+      const int64_t Ki = h_K[k];
+      const ST B = (ST)a.p * (ST)Ki;
+      ST bsc = 0;
+      int32_t bc = INT32_MAX;
+      int64_t kid = 0;
+      for (unsigned u = threadIdx.x; u < nused; u += blockDim.x) {
+        const uint32_t sl = used[u];
+        const int32_t c = keys[sl];
+        const int64_t v = (int64_t)vals[sl];
+        keys[sl] = LEIDEN_EMPTY_KEY;   // reset on read: clean for the next vertex
+        vals[sl] = 0;
+        ncand++;
+        if (c == d) { kid = v; continue; }
+        const ST sc = A * (ST)v - B * (ST)a.Sig[c];
+        if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
       }
 #pragma unroll
-      for (int u = 0; u < BLOCK_ROW_UNROLL; u++) {
-        const int32_t j = cc[u];
-        bool ok = j >= 0;
-        if (REFINE && ok && a.CB[j] != cbi) ok = false;
-        cc[u] = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
+      for (int o = 16; o > 0; o >>= 1) {
+        const ST osc = shfl_xor_any<ST>(bsc, o);
+        const int32_t oc = __shfl_xor_sync(FULL_MASK, bc, o);
+        kid += shfl_xor_i64(kid, o);
+        if (better(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
       }
+      if (lane == 0) { r_sc[warp] = bsc; r_c[warp] = bc; r_kid[warp] = kid; }
+      const int64_t Sd = h_Sd[k];
+      __syncthreads();
+      if (warp == 0) {
+        // the warps' bests, combined by warp 0 alone: the others go on to the
+        // next row (r_* are rewritten only after the next row's barrier)
+        bsc = lane < nwarp ? r_sc[lane] : (ST)0;
+        bc = lane < nwarp ? r_c[lane] : INT32_MAX;
+        kid = lane < nwarp ? r_kid[lane] : 0;
 #pragma unroll
-      for (int u = 0; u < BLOCK_ROW_UNROLL; u++) {
-        u64 sum = 0;
-        int slot = -1;
-        if (warp_combine((unsigned long long)(uint32_t)cc[u], cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum,
-                         wscratch[warp]))
-          slot = table_add_new(keys, vals, lh, cc[u], sum, &a.ctr[CTR_ERROR]);
-        list_new_slots(slot, used, &s_nused);
+        for (int o = 16; o > 0; o >>= 1) {
+          const ST osc = shfl_xor_any<ST>(bsc, o);
+          const int32_t oc = __shfl_xor_sync(FULL_MASK, bc, o);
+          kid += shfl_xor_i64(kid, o);
+          if (better(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
+        }
+        if (lane == 0) {
+          s_nused[par] = 0;   // for the row after next
+          bool propose = false;
+          i128 S = 0;
+          if (bc != INT32_MAX) {
+            S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - (ASYNC ? a.Sig[d] : Sd));
+            propose = S > 0;
+            if (REFINE && propose && a.C[bc] != bc) propose = false;
+          }
+          if (ASYNC) {
+            if (propose) propose = commit_async<REFINE>(a, i, d, bc);
+            if (propose) { accS += S; nmoves++; }
+          } else if (propose) {
+            const u64 slot = atomicAdd(a.prop_count, 1ull);
+            a.prop_i[slot] = i;
+            a.prop_c[slot] = bc;
+            a.prop_S[slot] = S;
+            if (REFINE) a.stamp[i] = a.stamp_val;
+          }
+          s_mv = propose;
+        }
+      }
+      if (ASYNC && !REFINE) {
+        __syncthreads();
+        if (s_mv)
+          for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) a.processed[a.g.idx[e]] = 0;
       }
     }
-    if (threadIdx.x == 0) { scanned += e1 - e0; nvert++; }
-    __syncthreads();
-    const unsigned nused = s_nused;
-    const ST A = (ST)a.A;
-    const int64_t Ki = s_K;
-    const ST B = (ST)a.p * (ST)Ki;
-    ST bsc = 0;
-    int32_t bc = INT32_MAX;
-    int64_t kid = 0;
-    for (unsigned u = threadIdx.x; u < nused; u += blockDim.x) {
-      const uint32_t sl = used[u];
-      const int32_t c = keys[sl];
-      const int64_t v = (int64_t)vals[sl];
-      keys[sl] = LEIDEN_EMPTY_KEY;   // reset on read: clean for the next vertex
-      vals[sl] = 0;
-      ncand++;
-      if (c == d) { kid = v; continue; }
-      const ST sc = A * (ST)v - B * (ST)a.Sig[c];
-      if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const ST osc = shfl_xor_any<ST>(bsc, o);
-      const int32_t oc = __shfl_xor_sync(FULL_MASK, bc, o);
-      kid += shfl_xor_i64(kid, o);
-      if (better(osc, oc, bsc, bc)) { bsc = osc; bc = oc; }
-    }
-    if (lane == 0) { r_sc[warp] = bsc; r_c[warp] = bc; r_kid[warp] = kid; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_nused = 0;
-      for (int k = 1; k < nwarp; k++) {
-        kid += r_kid[k];
-        if (better(r_sc[k], r_c[k], bsc, bc)) { bsc = r_sc[k]; bc = r_c[k]; }
-      }
-      bool propose = false;
-      i128 S = 0;
-      if (bc != INT32_MAX) {
-        S = (i128)bsc - (i128)a.A * kid - (i128)a.p * Ki * (Ki - (ASYNC ? a.Sig[d] : s_Sd));
-        propose = S > 0;
-        if (REFINE && propose && a.C[bc] != bc) propose = false;
-      }
-      if (ASYNC) {
-        if (propose) propose = commit_async<REFINE>(a, i, d, bc);
-        if (propose) { accS += S; nmoves++; }
-      } else if (propose) {
-        const u64 slot = atomicAdd(a.prop_count, 1ull);
-        a.prop_i[slot] = i;
-        a.prop_c[slot] = bc;
-        a.prop_S[slot] = S;
-        if (REFINE) a.stamp[i] = a.stamp_val;
-      }
-      s_mv = propose;
-    }
-    __syncthreads();
-    if (ASYNC && !REFINE && s_mv)
-      for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) a.processed[a.g.idx[e]] = 0;
-    __syncthreads();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -753,7 +789,7 @@ static void launch_group_k(const Tier &t, const MoveArgs<WT> &a, int sms, cudaSt
   ensure_smem((const void *)k, smem);
   const int64_t groups_per_block = (threads / 32) * (32 / G);
   int64_t blocks = (a.list_n + groups_per_block - 1) / groups_per_block;
-  const int64_t cap = (int64_t)sms * 16;
+  const int64_t cap = resident_blocks((const void *)k, threads, smem, sms);
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   LK_COUNTED k<<<(unsigned)blocks, threads, smem, s>>>(a);
@@ -798,11 +834,13 @@ void launch_decide(const Tier &t, const MoveArgs<WT> &a, int sms, cudaStream_t s
   // the warps' combine scratch
   const size_t smem = (size_t)(1u << log2H) * (sizeof(typename TableVal<ST>::type) + sizeof(int32_t)) +
                       (size_t)(1u << log2H) + (size_t)(t.threads / 32) * 32 * sizeof(u64);
-  int64_t blocks = a.list_n;
-  const int64_t cap = (int64_t)sms * 8;
-  if (blocks > cap) blocks = cap;
   auto k = decide_block<REFINE, ASYNC, WT, ST>;
   ensure_smem((const void *)k, smem);
+  // one listed vertex per block at a time: as many blocks as fit on the SMs
+  // at once (more would run as a partial second wave of grid-stride shares)
+  int64_t blocks = a.list_n;
+  const int64_t cap = resident_blocks((const void *)k, t.threads, smem, sms);
+  if (blocks > cap) blocks = cap;
   LK_COUNTED k<<<(unsigned)blocks, t.threads, smem, s>>>(a, log2H);
 }
 

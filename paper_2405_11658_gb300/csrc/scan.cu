@@ -26,6 +26,38 @@ void ensure_smem(const void *func, size_t bytes) {
     have = bytes;
 }
 
+int64_t resident_blocks(const void *func, int threads, size_t smem, int sms) {
+  struct Key {
+    const void *f;
+    int t;
+    size_t m;
+    bool operator==(const Key &o) const { return f == o.f && t == o.t && m == o.m; }
+  };
+  struct Hash {
+    size_t operator()(const Key &k) const {
+      return std::hash<const void *>()(k.f) ^ ((size_t)k.t << 20) ^ (k.m << 1);
+    }
+  };
+  static std::mutex mu;
+  static std::unordered_map<Key, int, Hash> per_sm;
+  int nb = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = per_sm.find(Key{func, threads, smem});
+    if (it != per_sm.end()) {
+      nb = it->second;
+    } else {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        nb = 0;
+      }
+      if (nb < 1) nb = 1;
+      per_sm[Key{func, threads, smem}] = nb;
+    }
+  }
+  return (int64_t)nb * sms;
+}
+
 static constexpr int SCAN_THREADS = 256;
 static constexpr int SCAN_ITEMS = 8;
 static constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
