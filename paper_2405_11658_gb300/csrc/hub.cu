@@ -117,24 +117,24 @@ __device__ __forceinline__ int64_t find_item(const int64_t *offs, int64_t n, int
   return lo;
 }
 
+// Insert of one (community, weight) into a hub's global table, starting with
+// the compare-and-swap of the home slot (one round trip for a new key or a
+// key already there; the probe sequence only after a collision).
 template <typename VT>
-__device__ __forceinline__ void hub_table_add(int32_t *keys, VT *vals, uint64_t t, int32_t c, u64 w, u64 *err) {
+__device__ __forceinline__ void hub_table_add_cas(int32_t *keys, VT *vals, uint64_t t, int32_t c, u64 w,
+                                                  u64 *err) {
   uint64_t s = ((uint64_t)hash32(c) * t) >> 32;
   for (uint64_t probe = 0; probe < t; probe++) {
-    const int32_t k = *(volatile int32_t *)&keys[s];
-    if (k == c) { add_val(&vals[s], w); return; }
-    if (k == LEIDEN_EMPTY_KEY) {
-      const int32_t old = atomicCAS(&keys[s], LEIDEN_EMPTY_KEY, c);
-      if (old == LEIDEN_EMPTY_KEY || old == c) { add_val(&vals[s], w); return; }
-    }
+    const int32_t old = atomicCAS(&keys[s], LEIDEN_EMPTY_KEY, c);
+    if (old == LEIDEN_EMPTY_KEY || old == c) { add_val(&vals[s], w); return; }
     s = s + 1 == t ? 0 : s + 1;
   }
   atomicOr(err, 16ull);
 }
 
-
 template <typename WT, typename VT>
 __global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine, HubWork hw) {
+  constexpr int U = LK_HUB_UNROLL;
   __shared__ u64 wscratch[8][32];
   const int64_t nitems = hw.tot[1];
   for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
@@ -148,20 +148,42 @@ __global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine,
     VT *vals = reinterpret_cast<VT *>(a.gvals) + hw.toff[k];
     const int32_t cbi = refine ? a.CB[i] : 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t cb = c0 + 32 * warp; cb < c1; cb += blockDim.x) {  // warp-uniform chunks
-      const int64_t e = cb + lane;
-      int32_t c = LEIDEN_EMPTY_KEY;
-      u64 wv = 0;
-      if (e < c1) {
-        const int32_t j = a.g.idx[e];
-        bool ok = j != i;
-        if (ok && (uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); ok = false; }
-        if (refine && ok && a.CB[j] != cbi) ok = false;
-        if (ok) { c = a.C[j]; wv = (u64)(int64_t)a.g.w[e]; }
+    // U warp-uniform 32-entry chunks per step, blockDim.x apart
+    for (int64_t cb = c0 + 32 * warp; cb < c1; cb += (int64_t)blockDim.x * U) {
+      int32_t cc[U];
+      u64 wv[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int64_t e = cb + (int64_t)u * blockDim.x + lane;
+        int32_t j = -1;
+        wv[u] = 0;
+        if (e < c1) {
+          j = a.g.idx[e];
+          wv[u] = (u64)(int64_t)a.g.w[e];
+          if (j == i) j = -1;
+          else if ((uint32_t)j >= (uint32_t)a.g.n) { atomicOr(&a.ctr[CTR_ERROR], 64ull); j = -1; }
+        }
+        cc[u] = j;
       }
-      u64 sum = 0;
-      if (warp_combine((unsigned long long)(uint32_t)c, c != LEIDEN_EMPTY_KEY, wv, &sum, wscratch[warp]))
-        hub_table_add(keys, vals, (uint64_t)t, c, sum, &a.ctr[CTR_ERROR]);
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int32_t j = cc[u];
+        bool ok = j >= 0;
+        if (refine && ok && a.CB[j] != cbi) ok = false;
+        cc[u] = ok ? a.C[j] : LEIDEN_EMPTY_KEY;
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        u64 sum = 0;
+        if (warp_combine((unsigned long long)(uint32_t)cc[u], cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum,
+                         wscratch[warp]))
+          wv[u] = sum;
+        else
+          cc[u] = LEIDEN_EMPTY_KEY;
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (cc[u] != LEIDEN_EMPTY_KEY) hub_table_add_cas(keys, vals, (uint64_t)t, cc[u], wv[u], &a.ctr[CTR_ERROR]);
     }
   }
 }
@@ -551,8 +573,11 @@ void launch_hubs(const MoveArgs<WT> &a, const HubWork &hw, int sms, cudaStream_t
     note_launch();
     cudaLaunchKernelEx(&cfg, hub_cluster_k<WT, ST, REFINE, ASYNC>, a, hw);
   }
-  LK_COUNTED hub_insert_k<WT, typename TableVal<ST>::type><<<sms * 8, 256, 0, s>>>(a, REFINE, hw);
-  LK_COUNTED hub_scan_k<WT, ST><<<sms * 8, 256, 0, s>>>(a, hw);
+  // grid-stride over equal work items: exactly the resident blocks
+  auto ins = hub_insert_k<WT, typename TableVal<ST>::type>;
+  auto scn = hub_scan_k<WT, ST>;
+  LK_COUNTED ins<<<(unsigned)resident_blocks((const void *)ins, 256, 0, sms), 256, 0, s>>>(a, REFINE, hw);
+  LK_COUNTED scn<<<(unsigned)resident_blocks((const void *)scn, 256, 0, sms), 256, 0, s>>>(a, hw);
   LK_COUNTED hub_final_k<WT, ST, REFINE, ASYNC><<<(unsigned)((a.list_n + 255) / 256), 256, 0, s>>>(a, hw);
 }
 

@@ -159,6 +159,15 @@ static constexpr int64_t HUB_TABLE_MIN = 4096;
 #ifndef LK_ROW_UNROLL
 #define LK_ROW_UNROLL 1
 #endif
+// Row entries per lane in flight in the block-tier decide kernel.
+#ifndef LK_BLOCK_ROW_UNROLL
+#define LK_BLOCK_ROW_UNROLL 4
+#endif
+// 32-entry chunks of a hub row a warp loads before it inserts them (their
+// row loads, C'[j] gathers and first table probes all in flight together).
+#ifndef LK_HUB_UNROLL
+#define LK_HUB_UNROLL 1
+#endif
 // Resident blocks per SM the group-tier decide kernels are compiled for (a
 // register cap for 256-thread blocks); 0 leaves the register count to the
 // compiler.

@@ -51,7 +51,7 @@ __device__ __forceinline__ void table_add(int32_t *keys, VT *vals, int log2H, in
 // issued together, so the gathers overlap instead of running back to back.
 static constexpr int SCAN_UNROLL = LK_SCAN_UNROLL;
 static constexpr int ROW_UNROLL = LK_ROW_UNROLL;  // row entries per lane in flight in the group kernels
-static constexpr int BLOCK_ROW_UNROLL = 1;        // ... and in the block kernels (4 measured slower)
+static constexpr int BLOCK_ROW_UNROLL = LK_BLOCK_ROW_UNROLL;  // ... and in the block kernels
 // Vertices per SM below which a whole-warp group tier runs as 4-warp blocks.
 static constexpr int64_t SMALL_WAVE_VERTICES = 16;
 template <typename ST, typename VT>
