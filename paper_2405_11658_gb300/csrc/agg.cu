@@ -201,32 +201,107 @@ __global__ void __launch_bounds__(256) agg_warp_k(GraphView<WT> g, const int32_t
   }
 }
 
-// Block tier: one block per community, table of 2^log2H shared slots.
+// Block tier: one block per community, table of 2^log2H shared slots.  The
+// community's member rows are walked as one flat range spread over all the
+// block's threads (a community of a few long super-vertex rows keeps every
+// warp busy): up to blockDim.x members at a time, their row starts and the
+// inclusive prefix of their degrees in shared memory, each thread finding
+// the member of its entry by a binary search over the prefix, AGG_UNROLL
+// entries per thread with their idx and C' loads in flight together.
+static constexpr int AGG_BLOCK_MAXT = 512;
 template <typename WT>
-__global__ void __launch_bounds__(512) agg_block_k(GraphView<WT> g, const int32_t *C, const int32_t *list,
+__global__ void __launch_bounds__(AGG_BLOCK_MAXT) agg_block_k(GraphView<WT> g, const int32_t *C, const int32_t *list,
                                                    int64_t nlist, const int64_t *coff, const int64_t *hoff,
                                                    const int32_t *cv, int32_t *hidx, int64_t *hw,
                                                    int64_t *cdist, int64_t *Kout, int log2H, u64 *err) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int H = 1 << log2H;
+  // dynamic shared memory: the table (2^log2H values, then keys), then per
+  // thread a member row start and degree prefix, then the warps' scratch
+  const int nt = blockDim.x;
   u64 *vals = reinterpret_cast<u64 *>(smem);
   int32_t *keys = reinterpret_cast<int32_t *>(vals + H);
+  int64_t *m_rs = reinterpret_cast<int64_t *>(keys + H);   // row start of each member of the batch
+  int64_t *m_incl = m_rs + nt;                             // inclusive prefix of their degrees
+  u64 (*wscratch)[32] = reinterpret_cast<u64 (*)[32]>(m_incl + nt);
   __shared__ unsigned long long s_cnt;
   __shared__ int64_t s_ws;
-  __shared__ u64 wscratch[16][32];
-  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __shared__ int64_t w_tot[AGG_BLOCK_MAXT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int64_t li = blockIdx.x; li < nlist; li += gridDim.x) {
     const int32_t c = list[li];
     const int64_t td = hoff[c + 1] - hoff[c];
     int lh = 1;
     while (lh < log2H && ((int64_t)1 << lh) < 2 * td) lh++;
     const int Hc = 1 << lh;
-    for (int s = threadIdx.x; s < Hc; s += blockDim.x) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
+    for (int s = threadIdx.x; s < Hc; s += nt) { keys[s] = LEIDEN_EMPTY_KEY; vals[s] = 0; }
     if (threadIdx.x == 0) { s_cnt = 0; s_ws = 0; }
-    __syncthreads();
-    warp_rows_into_table(g, C, cv, coff[c] + 32 * warp, coff[c + 1], 32 * nwarp, keys, vals, Hc - 1,
-                         32 - lh, err, wscratch[warp]);
-    __syncthreads();
+    const int64_t mb0 = coff[c], mb1 = coff[c + 1];
+    for (int64_t mb = mb0; mb < mb1; mb += nt) {
+      const int64_t m = mb + threadIdx.x;
+      int64_t rs = 0, deg = 0;
+      if (m < mb1) {
+        const int32_t v = cv[m];
+        rs = g.off[v];
+        deg = g.off[v + 1] - rs;
+      }
+      int64_t x = deg;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = shfl_i64(x, (lane - o) & 31);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) w_tot[warp] = x;
+      __syncthreads();   // also: the table is clear, the previous batch is done
+      int64_t pre = 0, total = 0;
+      for (int q = 0; q < nwarp; q++) {
+        const int64_t tq = w_tot[q];
+        if (q < warp) pre += tq;
+        total += tq;
+      }
+      m_rs[threadIdx.x] = rs;
+      m_incl[threadIdx.x] = pre + x;
+      const int nm = (int)(mb1 - mb < nt ? mb1 - mb : nt);
+      __syncthreads();
+      for (int64_t t0 = 0; t0 < total; t0 += (int64_t)nt * AGG_UNROLL) {  // uniform over the block
+        int32_t jj[AGG_UNROLL];
+        u64 wv[AGG_UNROLL];
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) {
+          const int64_t t = t0 + (int64_t)u * nt + threadIdx.x;
+          jj[u] = -1;
+          wv[u] = 0;
+          if (t < total) {
+            // first member whose inclusive prefix exceeds t
+            int lo = 0, hi = nm - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (m_incl[mid] > t) hi = mid; else lo = mid + 1;
+            }
+            const int64_t before = lo ? m_incl[lo - 1] : 0;
+            const int64_t e = m_rs[lo] + (t - before);
+            jj[u] = g.idx[e];
+            wv[u] = (u64)(int64_t)g.w[e];
+          }
+        }
+        int32_t cc[AGG_UNROLL];
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) {
+          const bool ok = (uint32_t)jj[u] < (uint32_t)g.n;
+          if (!ok && jj[u] != -1) atomicOr(err, 64ull);
+          cc[u] = ok ? C[jj[u]] : LEIDEN_EMPTY_KEY;
+        }
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) {
+          u64 sum = 0;
+          if (warp_combine((unsigned long long)(uint32_t)cc[u], cc[u] != LEIDEN_EMPTY_KEY, wv[u], &sum,
+                           wscratch[warp]))
+            tadd(keys, vals, Hc - 1, 32 - lh, cc[u], sum, err);
+        }
+      }
+      __syncthreads();   // the batch's prefix is read before the next one is written
+    }
+    if (mb0 == mb1) __syncthreads();
     warp_emit(keys, vals, Hc, 32 * warp, 32 * nwarp, hidx, hw, hoff[c], &s_cnt, &s_ws);
     __syncthreads();
     if (threadIdx.x == 0) { cdist[c] = (int64_t)s_cnt; Kout[c] = s_ws; }
@@ -699,10 +774,12 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
                                           wk.cdist, Kout, err);
       }
     } else if (T.kind == TIER_BLOCK) {
-      const size_t smem = (size_t)(1u << T.log2H) * 12;
+      // table, member batch (16 bytes a thread), combine scratch (256 bytes a warp)
+      const size_t smem = (size_t)(1u << T.log2H) * 12 + (size_t)T.threads * 16 + (size_t)(T.threads / 32) * 256;
       auto k = agg_block_k<WT>;
       ensure_smem((const void *)k, smem);
-      int64_t blocks = nl < (int64_t)wk.sms * 4 ? nl : (int64_t)wk.sms * 4;
+      const int64_t cap = resident_blocks((const void *)k, T.threads, smem, wk.sms);
+      int64_t blocks = nl < cap ? nl : cap;
       LK_COUNTED k<<<(unsigned)blocks, T.threads, smem, s>>>(g, C, list, nl, wk.coff, wk.hoff, wk.cv, wk.hidx, wk.hw,
                                                   wk.cdist, Kout, T.log2H, err);
     } else {

@@ -468,6 +468,7 @@ int refine(Run &r, GraphView<WT> g, const Buckets &b, bool all_changed, int64_t 
       launch_apply_refine(c->prop_i, c->prop_c, c->ctr, c->stamp, sv, c->Cp, c->Kp, c->Sp, c->sms, c->st);
     }
   }
+  if (async) launch_clear_left(c->Sp, g.n, c->st);
   cudaMemcpyAsync(c->h_ctr, c->ctr, CTR_COUNT * sizeof(u64), cudaMemcpyDeviceToHost, c->st);
   int rc = sync(c);
   if (rc) return rc;

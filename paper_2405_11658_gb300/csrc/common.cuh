@@ -76,6 +76,36 @@ __device__ __forceinline__ void atomic_add_i64(int64_t *p, int64_t v) {
   atomicAdd((u64 *)p, (u64)v);
 }
 
+// ASYNC refinement (Alg. leidenre with the paper's in-place updates): singleton
+// i leaves its own community for c.  i leaves only while still isolated
+// (Sigma'[i] = K'[i]); its total then holds REFINE_LEFT, far below any sum of
+// degrees, for the rest of the phase, so a vertex about to join i's community
+// sees a negative total and undoes its step -- however many other joiners are
+// adding and undoing at the same moment.  (Marking with 0 is not enough: a
+// second joiner's add, not yet undone, can hide it from a third, which would
+// then join a community whose own vertex has left.)  Returns true once i is in
+// c; the caller writes C'[i].  A sub-community never loses the vertex it is
+// named after, so every member stays connected to it.
+static constexpr int64_t REFINE_LEFT = INT64_MIN / 2;
+// Sigma'[c] as a score reads it: a community whose own vertex has left
+// (ASYNC refinement) counts as empty, and its marker never enters a product.
+__device__ __forceinline__ int64_t sigma_for_score(const int64_t *Sig, int32_t c) {
+  const int64_t v = Sig[c];
+  return v < 0 ? 0 : v;
+}
+__device__ __forceinline__ bool refine_join_async(int64_t *Sig, int32_t i, int64_t Ki, int32_t c) {
+  if ((int64_t)atomicCAS((unsigned long long *)&Sig[i], (unsigned long long)Ki,
+                         (unsigned long long)REFINE_LEFT) != Ki)
+    return false;
+  const int64_t prev = (int64_t)atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)Ki);
+  if (prev < 0) {  // c's own vertex has left: undo both steps and stay
+    atomic_add_i64(&Sig[c], -Ki);
+    atomic_add_i64(&Sig[i], Ki - REFINE_LEFT);
+    return false;
+  }
+  return true;
+}
+
 // Warp-aggregated reservation of `want` (0/1 per lane) slots in a counter;
 // returns this lane's slot (valid where want != 0).  Whole warp must call.
 __device__ __forceinline__ u64 warp_reserve(u64 *counter, bool want) {

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256) hub_scan_k(MoveArgs<WT> a, HubWork hw) {
       vals[s] = 0;
       cand++;
       if (c == d) { kid = v; continue; }
-      const ST sc = A * (ST)v - B * (ST)a.Sig[c];
+      const ST sc = A * (ST)v - B * (ST)sigma_for_score(a.Sig, c);
       if (hub_better<WT, ST>(sc, c, bsc, bc)) { bsc = sc; bc = c; }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -282,18 +282,8 @@ __global__ void __launch_bounds__(256) hub_final_k(MoveArgs<WT> a, HubWork hw) {
         const u64 slot = atomicAdd(&a.ctr[CTR_BIG], 1ull);
         a.big[slot] = i;
       } else {
-        ok = false;
-        const u64 old = atomicCAS((u64 *)&a.Sig[i], (u64)Ki, 0ull);
-        if ((int64_t)old == Ki) {
-          const u64 prev = atomicAdd((u64 *)&a.Sig[bc], (u64)Ki);
-          if (prev == 0ull) {
-            atomic_add_i64(&a.Sig[bc], -Ki);
-            atomic_add_i64(&a.Sig[i], Ki);
-          } else {
-            a.C[i] = bc;
-            ok = true;
-          }
-        }
+        ok = refine_join_async(a.Sig, i, Ki, bc);
+        if (ok) a.C[i] = bc;
       }
       if (ok) {
         atomicAdd(&a.ctr[CTR_MOVES], 1ull);
@@ -404,7 +394,7 @@ __global__ void __launch_bounds__(HC_THREADS) hub_cluster_k(MoveArgs<WT> a, HubW
       const int64_t v = (int64_t)vals[sl];
       cand++;
       if (c == d) { kid = v; continue; }
-      const ST sc = A * (ST)v - B * (ST)a.Sig[c];
+      const ST sc = A * (ST)v - B * (ST)sigma_for_score(a.Sig, c);
       if (hub_better<WT, ST>(sc, c, bsc, bc)) { bsc = sc; bc = c; }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -457,18 +447,8 @@ __global__ void __launch_bounds__(HC_THREADS) hub_cluster_k(MoveArgs<WT> a, HubW
             a.big[slot] = i;
           }
         } else {
-          ok = false;
-          const u64 old = atomicCAS((u64 *)&a.Sig[i], (u64)Ki, 0ull);
-          if ((int64_t)old == Ki) {
-            const u64 prev = atomicAdd((u64 *)&a.Sig[bc], (u64)Ki);
-            if (prev == 0ull) {
-              atomic_add_i64(&a.Sig[bc], -Ki);
-              atomic_add_i64(&a.Sig[i], Ki);
-            } else {
-              a.C[i] = bc;
-              ok = true;
-            }
-          }
+          ok = refine_join_async(a.Sig, i, Ki, bc);
+          if (ok) a.C[i] = bc;
         }
         if (ok) {
           atomicAdd(&a.ctr[CTR_MOVES], 1ull);

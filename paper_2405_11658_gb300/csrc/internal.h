@@ -234,6 +234,7 @@ void launch_iota(int32_t *a, int64_t n, cudaStream_t s);
 void launch_fill_u8(uint8_t *a, uint8_t v, int64_t n, cudaStream_t s);
 void launch_copy_i64(int64_t *dst, const int64_t *src, int64_t n, cudaStream_t s);
 void launch_invert_u8(uint8_t *dst, const uint8_t *src, int64_t n, cudaStream_t s);
+void launch_clear_left(int64_t *Sig, int64_t n, cudaStream_t s);
 void launch_sum_i64(const int64_t *a, int64_t n, u64 *out, cudaStream_t s);
 void launch_subset_renumber(int64_t n, int32_t *C, const int64_t *Sig, int64_t *Sig2,
                             const uint8_t *ch, uint8_t *ch2, int32_t *rep, cudaStream_t s);

@@ -53,6 +53,12 @@ void launch_copy_i64(int64_t *dst, const int64_t *src, int64_t n, cudaStream_t s
   if (n > 0) cudaMemcpyAsync(dst, src, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
 }
 __global__ void invert_u8_k(uint8_t *d, const uint8_t *a, int64_t n) { GRID_STRIDE(i, n) d[i] = a[i] ? 0 : 1; }
+// After an ASYNC refinement: the totals of communities whose own vertex left
+// hold the departure marker; those communities are empty.
+__global__ void clear_left_k(int64_t *Sig, int64_t n) { GRID_STRIDE(i, n) if (Sig[i] < 0) Sig[i] = 0; }
+void launch_clear_left(int64_t *Sig, int64_t n, cudaStream_t s) {
+  if (n > 0) LK_COUNTED clear_left_k<<<grid_for(n, 256), 256, 0, s>>>(Sig, n);
+}
 void launch_invert_u8(uint8_t *dst, const uint8_t *src, int64_t n, cudaStream_t s) {
   if (n > 0) LK_COUNTED invert_u8_k<<<grid_for(n, 256), 256, 0, s>>>(dst, src, n);
 }

@@ -69,7 +69,7 @@ __device__ __forceinline__ void scan_slots(const int32_t *keys, const VT *vals, 
     }
 #pragma unroll
     for (int u = 0; u < SCAN_UNROLL; u++)
-      sg[u] = (ck[u] != LEIDEN_EMPTY_KEY && ck[u] != d) ? Sig[ck[u]] : 0;
+      sg[u] = (ck[u] != LEIDEN_EMPTY_KEY && ck[u] != d) ? sigma_for_score(Sig, ck[u]) : 0;
 #pragma unroll
     for (int u = 0; u < SCAN_UNROLL; u++) {
       const int32_t c = ck[u];
@@ -112,19 +112,7 @@ __device__ __forceinline__ bool commit_async(const MoveArgs<WT> &a, int32_t i, i
     if (a.dynamic) { a.changed[d] = 1; a.changed[c] = 1; }
     return true;
   } else {
-    // atomicCAS(Sigma'[i], K'[i], 0): i leaves only while still isolated.
-    u64 old = atomicCAS((u64 *)&a.Sig[i], (u64)Ki, 0ull);
-    if ((int64_t)old != Ki) return false;
-    // Join c*.  A total of 0 means c*'s own vertex has just left in the same
-    // way (a vertex with an edge has K > 0): undo both steps and stay, so a
-    // sub-community never loses the vertex it is named after and every
-    // member stays adjacent to it.
-    const u64 prev = atomicAdd((u64 *)&a.Sig[c], (u64)Ki);
-    if (prev == 0ull) {
-      atomic_add_i64(&a.Sig[c], -Ki);
-      atomic_add_i64(&a.Sig[i], Ki);
-      return false;
-    }
+    if (!refine_join_async(a.Sig, i, Ki, c)) return false;
     a.C[i] = c;
     return true;
   }
@@ -228,7 +216,7 @@ __global__ void LK_GROUP_BOUNDS decide_group(MoveArgs<WT> a) {
         if (c == d) {
           kid = (int64_t)sum;
         } else {
-          const ST sc = (ST)a.A * (ST)(int64_t)sum - (ST)a.p * (ST)Ki * (ST)a.Sig[c];
+          const ST sc = (ST)a.A * (ST)(int64_t)sum - (ST)a.p * (ST)Ki * (ST)sigma_for_score(a.Sig, c);
           bsc = sc;
           bc = c;
         }
@@ -394,7 +382,7 @@ __global__ void __launch_bounds__(256) decide_thread(MoveArgs<WT> a) {
     }
     int64_t sg[KMAX];
 #pragma unroll
-    for (int k = 0; k < KMAX; k++) sg[k] = (cc[k] != LEIDEN_EMPTY_KEY && cc[k] != d) ? a.Sig[cc[k]] : 0;
+    for (int k = 0; k < KMAX; k++) sg[k] = (cc[k] != LEIDEN_EMPTY_KEY && cc[k] != d) ? sigma_for_score(a.Sig, cc[k]) : 0;
     const ST A = (ST)a.A;
     const ST B = (ST)a.p * (ST)Ki;
     ST bsc = 0;
@@ -622,7 +610,7 @@ __global__ void __launch_bounds__(1024) decide_block(MoveArgs<WT> a, int log2H) 
         vals[sl] = 0;
         ncand++;
         if (c == d) { kid = v; continue; }
-        const ST sc = A * (ST)v - B * (ST)a.Sig[c];
+        const ST sc = A * (ST)v - B * (ST)sigma_for_score(a.Sig, c);
         if (better(sc, c, bsc, bc)) { bsc = sc; bc = c; }
       }
 #pragma unroll
