@@ -26,7 +26,7 @@
 
 namespace lk {
 
-static constexpr int HUB_CHUNK = 4096;      // row entries per insert work item
+static constexpr int HUB_CHUNK = LK_HUB_CHUNK;  // row entries per insert work item
 static constexpr int HUB_SCAN_CHUNK = 4096; // table slots per scan work item
 
 template <typename WT>

@@ -165,6 +165,15 @@ static constexpr int64_t HUB_TABLE_MIN = 4096;
 #endif
 // 32-entry chunks of a hub row a warp loads before it inserts them (their
 // row loads, C'[j] gathers and first table probes all in flight together).
+// Row entries of one hub-insert work item.
+#ifndef LK_HUB_CHUNK
+#define LK_HUB_CHUNK 4096
+#endif
+// Movers with rows longer than this re-mark their neighbours through the
+// big-row kernel (spread over many blocks) instead of half a warp.
+#ifndef LK_BIG_ROW
+#define LK_BIG_ROW 4096
+#endif
 #ifndef LK_HUB_UNROLL
 #define LK_HUB_UNROLL 1
 #endif
@@ -200,7 +209,7 @@ void launch_apply_moves(const int32_t *prop_i, const int32_t *prop_c, const i128
                         const int32_t *idx, int32_t *big, int dynamic, int sms, cudaStream_t s);
 // Movers with more than BIG_ROW entries leave their neighbour re-marking
 // to launch_mark_big, which spreads each row over the whole grid.
-static constexpr int64_t BIG_ROW = 4096;
+static constexpr int64_t BIG_ROW = LK_BIG_ROW;
 void launch_mark_big(const int32_t *big, const u64 *count, const int64_t *off, const int32_t *idx,
                      uint8_t *processed, int sms, cudaStream_t s);
 // hub.cu
