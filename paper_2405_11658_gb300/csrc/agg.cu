@@ -8,9 +8,9 @@
 //    into a hashtable of (neighbour community d, summed weight); the entries
 //    land in the community's hole range and cdist[c] counts them.  Work is
 //    bucketed by total degree: a warp with a shared table, a block with a
-//    shared table, or many blocks sharing a table in global scratch for the
-//    largest communities (the load imbalance of selective refinement,
-//    Sec. 4.4);
+//    shared table, or, for the largest communities, their entries split by
+//    target into shared-memory-sized buckets hashed by many blocks (the load
+//    imbalance of selective refinement, Sec. 4.4);
 // 4. exclusive scan of cdist gives the compact super-vertex offsets; a copy
 //    removes the holes.
 // Row order inside the super-vertex graph is whatever the tables produced:
@@ -316,11 +316,11 @@ __global__ void __launch_bounds__(AGG_BLOCK_MAXT) agg_block_k(GraphView<WT> g, c
 // their member rows (count, scatter) plus one over the buckets (hash, emit):
 //   size:    P_k = power of two >= min(tdeg_k, |Gamma|) / BUCKET_KEYS buckets;
 //   count:   entries per bucket (warp-combined atomics);
-//   scan:    bucket offsets in the scratch array;
+//   scan:    bucket offsets in the scratch arrays (the output graph's idx and
+//            w arrays, free until the final compaction writes them);
 //   scatter: (target, weight) pairs into their bucket's range of the scratch;
-//   hash:    one block per bucket builds its table in shared memory, emits the
-//            distinct targets into the community's hole range and resets the
-//            scratch it read.
+//   hash:    one block per bucket builds its table in shared memory and emits
+//            the distinct targets into the community's hole range.
 // No hash table lives in DRAM, so no atomic has to go there.
 // ---------------------------------------------------------------------------
 static constexpr int BUCKET_KEYS = 4096;      // at most this many distinct targets per bucket, on average
@@ -462,8 +462,8 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
   }
 }
 
-// One block per bucket: hash the bucket's pairs in shared memory, emit the
-// distinct targets into the community's hole range, reset the scratch.  The
+// One block per bucket: hash the bucket's pairs in shared memory and emit the
+// distinct targets into the community's hole range.  The
 // table is cleared once per block; every bucket lists the slots it occupies
 // (one shared atomic per warp) and resets exactly those while emitting them,
 // so a bucket costs work in proportion to its pairs, not to the table size.
@@ -501,8 +501,8 @@ __device__ __forceinline__ BucketInfo bucket_info(int64_t bk, const int32_t *lis
 }
 
 __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, const int32_t *bown, const int64_t *nbk,
-                                                   const int64_t *bkoff, const int64_t *bpos, int32_t *skeys,
-                                                   u64 *svals, const u64 *selfw, const int64_t *hoff, int32_t *hidx,
+                                                   const int64_t *bkoff, const int64_t *bpos, const int32_t *skeys,
+                                                   const u64 *svals, const u64 *selfw, const int64_t *hoff, int32_t *hidx,
                                                    int64_t *hw, int64_t *cdist, int64_t *Kout, int64_t nb,
                                                    u64 *err) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -554,11 +554,6 @@ __global__ void __launch_bounds__(512) agg_bhash_k(const int32_t *list, const in
         dd[u] = LEIDEN_EMPTY_KEY;
         ww[u] = 0;
         if (pos < b.p1) { dd[u] = skeys[pos]; ww[u] = svals[pos]; }
-      }
-#pragma unroll
-      for (int u = 0; u < BH_UNROLL; u++) {
-        const int64_t pos = pb0 + 32 * u + lane;
-        if (pos < b.p1) { skeys[pos] = LEIDEN_EMPTY_KEY; svals[pos] = 0; }  // leave the scratch empty
       }
 #pragma unroll
       for (int u = 0; u < BH_UNROLL; u++) {
@@ -810,16 +805,18 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(wk.bcnt), wk.bpos, nb, wk.scan_tmp, s);
       cudaMemsetAsync(wk.bcnt, 0, (size_t)(nb + 1) * sizeof(u64), s);
       // the bucket ranges tile [0, sum of the listed total degrees) of the
-      // scratch arrays, which are empty on entry and left empty
+      // output graph's idx / w arrays, which the compaction below only writes
+      // after the buckets are hashed (the scratch needs no clearing then)
+      u64 *svals = reinterpret_cast<u64 *>(w2);
       LK_COUNTED agg_bpass_k<1, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
-                                               wk.bcnt, wk.bpos, wk.gkeys, wk.gvals, selfw, err);
+                                               wk.bcnt, wk.bpos, idx2, svals, selfw, err);
       const size_t smem = (size_t)BUCKET_SLOTS * (12 + 2);
       ensure_smem((const void *)agg_bhash_k, smem);
       // the bucket counters are free after the scatter: they hold the owners
       int32_t *bown = reinterpret_cast<int32_t *>(wk.bcnt);
       LK_COUNTED agg_bown_k<<<gridn(nl, 256), 256, 0, s>>>(bkoff, nl, bown);
-      LK_COUNTED agg_bhash_k<<<(unsigned)(wk.sms * 2), 512, smem, s>>>(list, bown, nbk, bkoff, wk.bpos, wk.gkeys,
-                                                            wk.gvals, selfw, wk.hoff, wk.hidx, wk.hw, wk.cdist, Kout,
+      LK_COUNTED agg_bhash_k<<<(unsigned)(wk.sms * 2), 512, smem, s>>>(list, bown, nbk, bkoff, wk.bpos, idx2,
+                                                            svals, selfw, wk.hoff, wk.hidx, wk.hw, wk.cdist, Kout,
                                                             nb, err);
     }
   }
