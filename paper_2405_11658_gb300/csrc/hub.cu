@@ -518,9 +518,12 @@ __global__ void __launch_bounds__(256) mark_big_rows_k(const int32_t *big, const
       int32_t j[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) j[u] = e + u * step < e1 ? idx[e + u * step] : -1;
+      uint8_t f[4];   // read before the store, as in the apply
+#pragma unroll
+      for (int u = 0; u < 4; u++) f[u] = j[u] >= 0 ? processed[j[u]] : 0;
 #pragma unroll
       for (int u = 0; u < 4; u++)
-        if (j[u] >= 0) processed[j[u]] = 0;
+        if (f[u]) processed[j[u]] = 0;
     }
   }
 }

@@ -159,6 +159,10 @@ static constexpr int64_t HUB_TABLE_MIN = 4096;
 #ifndef LK_ROW_UNROLL
 #define LK_ROW_UNROLL 1
 #endif
+// Neighbour re-marking of the DET apply: row entries per lane in flight.
+#ifndef LK_REMARK_UNROLL
+#define LK_REMARK_UNROLL 4
+#endif
 // Row entries per lane in flight in the block-tier decide kernel.
 #ifndef LK_BLOCK_ROW_UNROLL
 #define LK_BLOCK_ROW_UNROLL 4

@@ -451,7 +451,10 @@ __device__ i128 apply_moves(const Lvl<WT> &g, WS &w, const Ctl &ct, Shared &sm) 
       if (ct.dynamic) { w.ch[d] = 1; w.ch[c] = 1; }
       acc += w.pS[m];
     }
-    for (int64_t e = g.off[i] + lane; e < g.off[i + 1]; e += 32) w.proc[g.idx[e]] = 0;
+    for (int64_t e = g.off[i] + lane; e < g.off[i + 1]; e += 32) {
+      const int32_t j = g.idx[e];
+      if (w.proc[j]) w.proc[j] = 0;   // most are unprocessed already: spare the store
+    }
   }
   __syncthreads();
   return acc;
