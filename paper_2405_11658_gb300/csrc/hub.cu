@@ -132,8 +132,26 @@ __device__ __forceinline__ void hub_table_add_cas(int32_t *keys, VT *vals, uint6
   atomicOr(err, 16ull);
 }
 
+// With 32-bit table values (the 64-bit score path) a slot is one 64-bit word
+// of the value scratch: the key + 1 in its low half (0: empty, which is how
+// the scratch is left), the summed weight in its high half, so the
+// compare-and-swap of the key and the add of the weight touch the same DRAM
+// sector, and the drain reads one array instead of two.
+__device__ __forceinline__ void hub_table_add_packed(u64 *tab, uint64_t t, int32_t c, u64 w, u64 *err) {
+  const uint32_t key = (uint32_t)c + 1u;
+  uint64_t s = ((uint64_t)hash32(c) * t) >> 32;
+  for (uint64_t probe = 0; probe < t; probe++) {
+    uint32_t *slot = reinterpret_cast<uint32_t *>(&tab[s]);   // [0] key + 1, [1] weight
+    const uint32_t old = atomicCAS(slot, 0u, key);
+    if (old == 0u || old == key) { atomicAdd(slot + 1, (uint32_t)w); return; }
+    s = s + 1 == t ? 0 : s + 1;
+  }
+  atomicOr(err, 16ull);
+}
+
 template <typename WT, typename VT>
 __global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine, HubWork hw) {
+  constexpr bool PACKED = sizeof(VT) == 4;
   constexpr int U = LK_HUB_UNROLL;
   __shared__ u64 wscratch[8][32];
   const int64_t nitems = hw.tot[1];
@@ -182,8 +200,11 @@ __global__ void __launch_bounds__(256) hub_insert_k(MoveArgs<WT> a, bool refine,
           cc[u] = LEIDEN_EMPTY_KEY;
       }
 #pragma unroll
-      for (int u = 0; u < U; u++)
-        if (cc[u] != LEIDEN_EMPTY_KEY) hub_table_add_cas(keys, vals, (uint64_t)t, cc[u], wv[u], &a.ctr[CTR_ERROR]);
+      for (int u = 0; u < U; u++) {
+        if (cc[u] == LEIDEN_EMPTY_KEY) continue;
+        if (PACKED) hub_table_add_packed(a.gvals + hw.toff[k], (uint64_t)t, cc[u], wv[u], &a.ctr[CTR_ERROR]);
+        else hub_table_add_cas(keys, vals, (uint64_t)t, cc[u], wv[u], &a.ctr[CTR_ERROR]);
+      }
     }
   }
 }
@@ -213,12 +234,24 @@ __global__ void __launch_bounds__(256) hub_scan_k(MoveArgs<WT> a, HubWork hw) {
     ST bsc = 0;
     int32_t bc = INT32_MAX;
     int64_t kid = 0, cand = 0;
+    constexpr bool PACKED = sizeof(typename TableVal<ST>::type) == 4;
+    u64 *tab = a.gvals + hw.toff[k];
     for (int64_t s = s0 + threadIdx.x; s < s0 + HUB_SCAN_CHUNK; s += blockDim.x) {
-      const int32_t c = keys[s];
-      if (c == LEIDEN_EMPTY_KEY) continue;
-      const int64_t v = (int64_t)vals[s];
-      keys[s] = LEIDEN_EMPTY_KEY;  // reset for the next user of the scratch
-      vals[s] = 0;
+      int32_t c;
+      int64_t v;
+      if (PACKED) {
+        const u64 x = tab[s];
+        if (x == 0) continue;
+        c = (int32_t)((uint32_t)x - 1u);
+        v = (int64_t)(x >> 32);
+        tab[s] = 0;                  // reset for the next user of the scratch
+      } else {
+        c = keys[s];
+        if (c == LEIDEN_EMPTY_KEY) continue;
+        v = (int64_t)vals[s];
+        keys[s] = LEIDEN_EMPTY_KEY;  // reset for the next user of the scratch
+        vals[s] = 0;
+      }
       cand++;
       if (c == d) { kid = v; continue; }
       const ST sc = A * (ST)v - B * (ST)sigma_for_score(a.Sig, c);
