@@ -80,8 +80,14 @@ void launch_sum_i64(const int64_t *a, int64_t n, u64 *out, cudaStream_t s) {
 __global__ void sr_init_k(int64_t n, int32_t *rep, int64_t *Sig2, uint8_t *ch2) {
   GRID_STRIDE(c, n) { rep[c] = INT_MAX; Sig2[c] = 0; ch2[c] = 0; }
 }
+// The minima only fall: a member that reads a representative already below
+// its own ID cannot lower it, and skips the atomic (a large community's
+// members would otherwise queue on one address).
 __global__ void sr_min_k(int64_t n, const int32_t *C, int32_t *rep) {
-  GRID_STRIDE(i, n) atomicMin(&rep[C[i]], (int32_t)i);
+  GRID_STRIDE(i, n) {
+    const int32_t c = C[i];
+    if (rep[c] > (int32_t)i) atomicMin(&rep[c], (int32_t)i);
+  }
 }
 __global__ void sr_move_k(int64_t n, const int32_t *rep, const int64_t *Sig, int64_t *Sig2,
                           const uint8_t *ch, uint8_t *ch2) {
@@ -121,7 +127,12 @@ void launch_break(int64_t n, int32_t *C, const int64_t *K, int64_t *Sig, const u
 }
 
 // Dense renumbering in increasing order of the old ID (flag + exclusive scan).
-__global__ void flag_k(int64_t n, const int32_t *C, uint8_t *ex) { GRID_STRIDE(i, n) ex[C[i]] = 1; }
+__global__ void flag_k(int64_t n, const int32_t *C, uint8_t *ex) {
+  GRID_STRIDE(i, n) {
+    const int32_t c = C[i];
+    if (!ex[c]) ex[c] = 1;   // most members find the flag set already: spare the store
+  }
+}
 __global__ void relabel_scan_k(int64_t n, int32_t *C, const int64_t *scanned) {
   GRID_STRIDE(i, n) C[i] = (int32_t)scanned[C[i]];
 }
@@ -148,7 +159,10 @@ __global__ void canon_init_k(int64_t n, int32_t *minv, uint8_t *flag) {
   GRID_STRIDE(i, n) { minv[i] = INT_MAX; flag[i] = 0; }
 }
 __global__ void canon_min_k(int64_t n, const int32_t *C, int32_t *minv) {
-  GRID_STRIDE(v, n) atomicMin(&minv[C[v]], (int32_t)v);
+  GRID_STRIDE(v, n) {
+    const int32_t c = C[v];
+    if (minv[c] > (int32_t)v) atomicMin(&minv[c], (int32_t)v);   // as in sr_min_k
+  }
 }
 __global__ void canon_flag_k(int64_t n, const int32_t *minv, uint8_t *flag) {
   GRID_STRIDE(c, n) if (minv[c] != INT_MAX) flag[minv[c]] = 1;
