@@ -22,6 +22,12 @@
 #include "common.cuh"
 #include "internal.h"
 
+// 1: the bucket path's count pass leaves each pair at its flat position and
+// the scatter streams them (0: the scatter walks the member rows again).
+#ifndef LK_AGG_PAIR_CACHE
+#define LK_AGG_PAIR_CACHE 1
+#endif
+
 namespace lk {
 
 static inline unsigned gridn(int64_t n, int threads, int64_t cap = 1 << 20) {
@@ -76,7 +82,7 @@ __device__ __forceinline__ void tadd(int32_t *keys, u64 *vals, uint32_t mask, in
 static constexpr int AGG_UNROLL = 4;
 template <typename WT, typename F>
 __device__ __forceinline__ void walk_segments(const GraphView<WT> &g, const int32_t *C, int64_t rs, int64_t cnt,
-                                              int64_t incl, int64_t total, u64 *err, F f) {
+                                              int64_t incl, int64_t total, u64 *err, F f, int64_t fbase = 0) {
   const int lane = threadIdx.x & 31;
   for (int64_t t0 = 0; t0 < total; t0 += 32 * AGG_UNROLL) {  // uniform per warp
     int32_t jj[AGG_UNROLL];
@@ -108,7 +114,11 @@ __device__ __forceinline__ void walk_segments(const GraphView<WT> &g, const int3
       cc[u] = ok ? C[jj[u]] : LEIDEN_EMPTY_KEY;
     }
 #pragma unroll
-    for (int u = 0; u < AGG_UNROLL; u++) f(cc[u], wv[u], cc[u] != LEIDEN_EMPTY_KEY);
+    for (int u = 0; u < AGG_UNROLL; u++) {
+      // the entry's position in the walked range (fbase + t), -1 past its end
+      const int64_t t = t0 + 32 * u + lane;
+      f(cc[u], wv[u], cc[u] != LEIDEN_EMPTY_KEY, t < total ? fbase + t : (int64_t)-1);
+    }
   }
 }
 
@@ -136,7 +146,7 @@ __device__ __forceinline__ void warp_rows_into_table(const GraphView<WT> &g, con
       if (lane >= o) incl += y;
     }
     const int64_t total = shfl_i64(incl, 31);
-    walk_segments(g, C, start, deg, incl, total, err, [&](int32_t c, u64 wv, bool act) {
+    walk_segments(g, C, start, deg, incl, total, err, [&](int32_t c, u64 wv, bool act, int64_t) {
       u64 sum = 0;
       if (warp_combine((unsigned long long)(uint32_t)c, act, wv, &sum, scratch)) tadd(keys, vals, mask, sh, c, sum, err);
     });
@@ -354,7 +364,7 @@ __global__ void agg_member_deg_k(GraphView<WT> g, const int32_t *cv, int64_t n, 
 // The warp walks the entries [w0, w1) of one community's flattened rows
 // (members cv[p_lo .. p_hi), pdeg = exclusive prefix of their degrees, so the
 // community's flat range starts at pdeg[p_lo]) and calls f(target, weight,
-// active) warp-uniformly, 32 entries at a time.
+// active, flat position) warp-uniformly, 32 entries at a time.
 template <typename WT, typename F>
 __device__ __forceinline__ void foreach_window(const GraphView<WT> &g, const int32_t *C, const int32_t *cv,
                                                const int64_t *pdeg, int64_t p_lo, int64_t p_hi, int64_t w0,
@@ -384,7 +394,9 @@ __device__ __forceinline__ void foreach_window(const GraphView<WT> &g, const int
       if (lane >= o) incl += y;
     }
     const int64_t total = shfl_i64(incl, 31);
-    walk_segments(g, C, rs, cnt, incl, total, err, f);
+    // the batch's clipped segments are consecutive in the flat range
+    const int64_t fb = pdeg[pb] > w0 ? pdeg[pb] : w0;
+    walk_segments(g, C, rs, cnt, incl, total, err, f, fb);
   }
 }
 
@@ -416,7 +428,7 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
                                                    const int64_t *bkoff, const int64_t *coff, const int64_t *hoff,
                                                    const int32_t *cv, const int64_t *pdeg, u64 *bcnt,
                                                    const int64_t *bpos, int32_t *skeys, u64 *svals, u64 *selfw,
-                                                   u64 *err) {
+                                                   u64 *err, int32_t *pk = nullptr, int64_t *pw = nullptr) {
   const int64_t nitems = wnoff[nlist];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ u64 wscr[8][32];  // blocks of 256 threads
@@ -428,7 +440,8 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
     const int64_t fw0 = hoff[c] + (it - wnoff[k]) * AGG_WINDOW;
     const int64_t fw1 = fw0 + AGG_WINDOW < hoff[c + 1] ? fw0 + AGG_WINDOW : hoff[c + 1];
     const int64_t P = nbk[k], base = bkoff[k];
-    foreach_window(g, C, cv, pdeg, coff[c], coff[c + 1], fw0, fw1, err, [&](int32_t d, u64 w, bool act0) {
+    foreach_window(g, C, cv, pdeg, coff[c], coff[c + 1], fw0, fw1, err, [&](int32_t d, u64 w, bool act0,
+                                                                             int64_t fpos) {
       const bool self = act0 && d == c;
       if (PASS == 0) {
         u64 sw = self ? w : 0;
@@ -440,6 +453,11 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
       u64 wsum = 0;
       const bool act = warp_combine((unsigned long long)(uint32_t)d, act0 && !self, w, &wsum, wscr[warp]);
       w = wsum;
+      if (PASS == 0 && pk && fpos >= 0) {
+        // the pair at its flat position, for the scatter (none: -1)
+        pk[fpos] = act ? d : LEIDEN_EMPTY_KEY;
+        pw[fpos] = act ? (int64_t)w : 0;
+      }
       const int64_t bk = act ? base + bucket_of(d, P) : -1;
       // lanes of the same bucket share one atomic
       const unsigned am = __ballot_sync(FULL_MASK, act);
@@ -459,6 +477,46 @@ __global__ void __launch_bounds__(256) agg_bpass_k(GraphView<WT> g, const int32_
       }
       __syncwarp();
     });
+  }
+}
+
+// Scatter of the pairs the count pass left at their flat positions: a
+// streamed read of them, instead of a second walk of the member rows with
+// their C'[j] gathers.  A warp takes 32 consecutive positions at a time.
+__global__ void __launch_bounds__(256) agg_bscatter_k(const int32_t *list, int64_t nlist, const int64_t *wnoff,
+                                                      const int64_t *nbk, const int64_t *bkoff,
+                                                      const int64_t *hoff, const int32_t *pk, const int64_t *pw,
+                                                      u64 *bcnt, const int64_t *bpos, int32_t *skeys,
+                                                      u64 *svals) {
+  const int64_t nitems = wnoff[nlist];
+  const int lane = threadIdx.x & 31;
+  const int64_t w0g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwg = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = w0g; it < nitems; it += nwg) {  // uniform per warp
+    const int64_t k = find_k(wnoff, nlist, it);
+    const int32_t c = list[k];
+    const int64_t fw0 = hoff[c] + (it - wnoff[k]) * AGG_WINDOW;
+    const int64_t fw1 = fw0 + AGG_WINDOW < hoff[c + 1] ? fw0 + AGG_WINDOW : hoff[c + 1];
+    const int64_t P = nbk[k], base = bkoff[k];
+    for (int64_t f0 = fw0; f0 < fw1; f0 += 32) {
+      const int64_t f = f0 + lane;
+      const int32_t d = f < fw1 ? pk[f] : LEIDEN_EMPTY_KEY;
+      const bool act = d != LEIDEN_EMPTY_KEY;
+      const u64 w = act ? (u64)pw[f] : 0;
+      const int64_t bk = act ? base + bucket_of(d, P) : -1;
+      const unsigned am = __ballot_sync(FULL_MASK, act);
+      if (act) {
+        const unsigned peers = __match_any_sync(am, (unsigned long long)bk);
+        const int leader = __ffs(peers) - 1;
+        u64 slot0 = 0;
+        if (lane == leader) slot0 = atomicAdd(&bcnt[bk], (u64)__popc(peers));
+        slot0 = __shfl_sync(peers, slot0, leader);
+        const int64_t pos = bpos[bk] + (int64_t)slot0 + __popc(peers & ((1u << lane) - 1u));
+        skeys[pos] = d;
+        svals[pos] = w;
+      }
+      __syncwarp();
+    }
   }
 }
 
@@ -800,16 +858,25 @@ int aggregate(GraphView<WT> g, const int32_t *C, int64_t nc, int64_t *off2, int3
       const unsigned grid = (unsigned)(wk.sms * 16);
       u64 *selfw = reinterpret_cast<u64 *>(wk.off2tmp + 4 * (nl + 1));   // [nl] internal weight
       cudaMemsetAsync(selfw, 0, (size_t)nl * sizeof(u64), s);
+      // the count pass leaves each entry's pair (after the warp combine) at its
+      // flat position in the communities' hole ranges of hidx / hw, which
+      // the bucket hash only writes afterwards
+      int32_t *pk = LK_AGG_PAIR_CACHE ? wk.hidx : nullptr;
+      int64_t *pw = LK_AGG_PAIR_CACHE ? wk.hw : nullptr;
       LK_COUNTED agg_bpass_k<0, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
-                                               wk.bcnt, nullptr, nullptr, nullptr, selfw, err);
+                                               wk.bcnt, nullptr, nullptr, nullptr, selfw, err, pk, pw);
       exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(wk.bcnt), wk.bpos, nb, wk.scan_tmp, s);
       cudaMemsetAsync(wk.bcnt, 0, (size_t)(nb + 1) * sizeof(u64), s);
       // the bucket ranges tile [0, sum of the listed total degrees) of the
       // output graph's idx / w arrays, which the compaction below only writes
       // after the buckets are hashed (the scratch needs no clearing then)
       u64 *svals = reinterpret_cast<u64 *>(w2);
-      LK_COUNTED agg_bpass_k<1, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv, pdeg,
-                                               wk.bcnt, wk.bpos, idx2, svals, selfw, err);
+      if (LK_AGG_PAIR_CACHE)
+        LK_COUNTED agg_bscatter_k<<<grid, 256, 0, s>>>(list, nl, wnoff, nbk, bkoff, wk.hoff, pk, pw, wk.bcnt, wk.bpos,
+                                                       idx2, svals);
+      else
+        LK_COUNTED agg_bpass_k<1, WT><<<grid, 256, 0, s>>>(g, C, list, nl, wnoff, nbk, bkoff, wk.coff, wk.hoff, wk.cv,
+                                                 pdeg, wk.bcnt, wk.bpos, idx2, svals, selfw, err);
       const size_t smem = (size_t)BUCKET_SLOTS * (12 + 2);
       ensure_smem((const void *)agg_bhash_k, smem);
       // the bucket counters are free after the scatter: they hold the owners
